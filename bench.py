@@ -1,0 +1,334 @@
+"""Benchmark: TFHE gate bootstrapping throughput on GB300 (gate bootstraps/s).
+
+Workload (one "step"): 65,536 independent NAND gate bootstraps, parameters n = 630,
+N = 1024, k = 1, Bgbit = 10, lg = 3, basebit = 2, t = 8, keys from seed 0 and inputs
+encrypting uniform bits under seed 1 -- the whole hot path per gate: pre-combination,
+modulus switch, blind rotation (630 CMux external products), sample extraction, key
+switch.  Keys and inputs are resident in HBM before the timed region; the inputs
+(2 x 165 MB per step) exceed the 129 MB L2.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+COUNT = 65536
+N_LWE, N_RING = 630, 1024
+# Algorithmic 32-bit modular multiplications per blind-rotation step of one ciphertext:
+# two NTT primes x (6 forward + 2 inverse length-1024 transforms x 5,120 butterflies +
+# 12 x 1,024 pointwise products) = 2 x 53,248.
+MODMUL_PER_STEP = 2 * ((6 + 2) * 5120 + 12 * 1024)
+# Peak modmul rate derived from unit counts and clocks: 152 SMs x 2,070 MHz x 64 integer
+# multiply-adds per SM per clock / 3 multiply-adds per Shoup modular multiplication.
+SMS, MAX_MHZ, IMAD_PER_CLK_SM, IMAD_PER_MODMUL = 152, 2070.0, 64, 3
+PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * IMAD_PER_CLK_SM / IMAD_PER_MODMUL
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dev(a):
+    import torch
+    a = np.ascontiguousarray(a)
+    return torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
+
+
+def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int = COUNT):
+    """Keys generated on the device from the seed-0 draws, inputs encrypted on the device."""
+    import torch
+    from paper_2407_19871_gb300 import build, locpir
+    build.build()
+    torch.cuda.set_device(local)
+    p = locpir.params_default()
+    d = synth.key_draws(seed_keys)
+    bsk = torch.empty(p.n * 6 * 2 * p.N, dtype=torch.int32, device="cuda")
+    ksk = torch.empty(p.N * 8 * 4 * (p.n + 1), dtype=torch.int32, device="cuda")
+    s_dev, S_dev = _dev(d.s), _dev(d.S)
+    locpir.lp_client_keygen_bsk(p, s_dev, S_dev, _dev(d.bsk_mask), _dev(d.bsk_noise), bsk)
+    locpir.lp_client_keygen_ksk(p, s_dev, S_dev, _dev(d.ksk_mask), _dev(d.ksk_noise), ksk)
+    ctx = locpir.Context(local)
+    ctx.lp_load_bsk_device(bsk)
+    ctx.lp_load_ksk_device(ksk)
+    del bsk, ksk
+    A, B = synth.nand_pairs(seed_inputs, count)
+    cts = []
+    for bits, off in ((A, 0), (B, count)):
+        dr = synth.lwe_draws(seed_inputs, count, offset=off)
+        out = torch.empty(count, p.n + 1, dtype=torch.int32, device="cuda")
+        mu = np.where(bits == 1, 1 << 29, (1 << 32) - (1 << 29)).astype(np.uint32)
+        locpir.lp_client_lwe_encrypt(p.n, s_dev, _dev(dr.mask), _dev(dr.noise), _dev(mu), out, count)
+        cts.append(out)
+    torch.cuda.synchronize()
+    return ctx, p, s_dev, (A, B), cts
+
+
+def check_outputs(p, s_dev, out, A, B) -> int:
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    ph = torch.empty(out.shape[0], dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, out.shape[0])
+    bits = (ph.cpu().numpy() > 0).astype(np.uint8)
+    return int((bits != (1 - (A & B))).sum())
+
+
+def cpu_baseline(seconds_target: float = 15.0) -> dict:
+    """The oracle as it stands, on all host cores, on the first S gates of the workload."""
+    import oracle
+    keys = oracle.keygen(synth.key_draws(0))
+    cores = oracle.threads()
+    A, B = synth.nand_pairs(1, COUNT)
+    # calibrate with one gate per core, then size the sample to ~seconds_target
+    S0 = cores
+    a = oracle.encrypt(keys.s, A[:S0], synth.lwe_draws(1, S0))
+    b = oracle.encrypt(keys.s, B[:S0], synth.lwe_draws(1, S0, offset=COUNT))
+    t0 = time.perf_counter()
+    oracle.gate_batch(keys, oracle.NAND, a, b, nthreads=cores)
+    dt0 = time.perf_counter() - t0
+    S = max(cores, min(COUNT, int(cores * max(1, round(seconds_target / max(dt0, 1e-3))))))
+    a = oracle.encrypt(keys.s, A[:S], synth.lwe_draws(1, S))
+    b = oracle.encrypt(keys.s, B[:S], synth.lwe_draws(1, S, offset=COUNT))
+    t0 = time.perf_counter()
+    oracle.gate_batch(keys, oracle.NAND, a, b, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": S / dt, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {S} of the 65,536 NAND gates (OpenMP over gates, {cores} threads), {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    keys = oracle.keygen(synth.key_draws(0))
+    cores = oracle.threads()
+    A, B = synth.nand_pairs(1, COUNT)
+    S = 2 * cores
+    a = oracle.encrypt(keys.s, A[:S], synth.lwe_draws(1, S))
+    b = oracle.encrypt(keys.s, B[:S], synth.lwe_draws(1, S, offset=COUNT))
+    for _ in range(args.warmup):
+        oracle.gate_batch(keys, oracle.NAND, a[:cores], b[:cores], nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gate_batch(keys, oracle.NAND, a, b, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = S * args.steps / dt
+    line = {"impl": "reference", "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "NAND gate bootstrapping, 65,536 gates (n=630, N=1024, Bgbit=10, lg=3, "
+                                   "basebit=2, t=8); each reference step a bounded sample"},
+            "cpu_baseline": {"value": value, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{S} of the 65,536 NAND gates per step (OpenMP, {cores} threads)"},
+            "e2e": {"value": value, "unit": "bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args) -> None:
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    rank, world, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(local)
+    out = torch.empty_like(a)
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx.lp_gate_batch(locpir.LP_NAND, a, b, None, out, COUNT, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    wrong = check_outputs(p, s_dev, out, A, B)
+
+    # ---- device-resident timed region
+    clocks = Clocks(local)
+    ctx.lp_reset_timing()
+    ctx.lp_set_timing(True)
+    launches0 = ctx.lp_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.lp_launch_count() - launches0
+    br_ms, br_n = ctx.lp_kernel_time("br")
+    ks_ms, ks_n = ctx.lp_kernel_time("ks")
+    ctx.lp_set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = COUNT * world * args.steps / (ms / 1e3)
+
+    # ---- end to end through the host-pointer entry point (pinned host buffers)
+    W = p.n + 1
+    ha = torch.empty(COUNT, W, dtype=torch.int32, pin_memory=True)
+    hb = torch.empty(COUNT, W, dtype=torch.int32, pin_memory=True)
+    ho = torch.empty(COUNT, W, dtype=torch.int32, pin_memory=True)
+    ha.copy_(a.cpu())
+    hb.copy_(b.cpu())
+    na, nb, no = ha.numpy().view(np.uint32), hb.numpy().view(np.uint32), ho.numpy().view(np.uint32)
+    ctx.lp_gate_batch_host(locpir.LP_NAND, na, nb, None, no, COUNT)  # warm the staging buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.lp_gate_batch_host(locpir.LP_NAND, na, nb, None, no, COUNT)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = COUNT * world * e2e_steps / e2e_s
+
+    # ---- per-gate path (same kernels, one gate per launch), on a sample
+    per_gate = None
+    if rank == 0 and args.per_gate > 0:
+        k = args.per_gate
+        torch.cuda.synchronize()
+        g0 = time.perf_counter()
+        for g in range(k):
+            ctx.lp_gate_batch(locpir.LP_NAND, a[g:g + 1], b[g:g + 1], None, out[g:g + 1], 1, st)
+            torch.cuda.synchronize()
+        per_gate = k / (time.perf_counter() - g0)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    br_avg_ms = br_ms / max(br_n, 1)
+    achieved = COUNT * N_LWE * MODMUL_PER_STEP / (br_avg_ms / 1e3)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("br_kernel_dram_bytes_per_launch")
+    except Exception:
+        traffic = None
+    line = {
+        "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "NAND gate bootstrapping: 65,536 independent gates per step (n=630, N=1024, k=1, "
+                               "Bgbit=10, lg=3, basebit=2, t=8; keys seed 0, inputs seed 1)",
+                   "global_batch": COUNT * world, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (2 x 165 MB per step)"},
+        "e2e": {"value": e2e_value, "unit": "bootstraps/s", "h2d_bytes_per_step": 2 * COUNT * W * 4,
+                "d2h_bytes_per_step": COUNT * W * 4},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "br_kernel (blind rotation + extraction)",
+                     "achieved": achieved / 1e12, "peak": PEAK_MODMUL_PER_S / 1e12, "unit": "Tmodmul/s",
+                     "frac": achieved / PEAK_MODMUL_PER_S, "traffic": traffic,
+                     "br_ms_per_launch": br_avg_ms, "ks_ms_per_launch": ks_ms / max(ks_n, 1)},
+        "clocks": clk,
+        "per_gate_bootstraps_per_s": per_gate,
+        "batched_speedup_vs_per_gate": (value / world / per_gate) if per_gate else None,
+        "decrypt_errors": wrong,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--per-gate", type=int, default=16, help="gates timed one per launch (0: skip)")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * locpir.h -- C-ABI of liblocpir.so: TFHE gate bootstrapping and the LocPIR circuits
+ * (LocPIR: Fast Private Location-based Information Retrieval over the Torus,
+ * arXiv 2407.19871) on one GB300 GPU.
+ *
+ * Conventions (every entry point):
+ *   - Torus32: uint32_t, the torus value x / 2^32 mod 1 (two's-complement wrap).
+ *   - LWE ciphertext: uint32_t[n + 1] = a[0 .. n-1], b; phase = b - <a, s>.  A batch is
+ *     [count][n + 1], contiguous.  Encoding f(m) = m/4 - 1/8: bit 1 -> 2^29, bit 0 -> -2^29
+ *     (Section 2.2, Encrypt / Decrypt).
+ *   - A coordinate is l ciphertexts, least significant bit first (index l-1 is the MSB that
+ *     Algorithm 2 flips).  A box is [4][l][n + 1] in the order X1, X2, Y1, Y2; the point
+ *     (x, y) is inside iff X1 <= x < X2 and Y1 <= y < Y2.  A service is [m][n + 1], bit 0
+ *     first.
+ *   - Pointers named *_dev and every ciphertext pointer of the batch calls are DEVICE
+ *     pointers on the context's device; `stream` is a cudaStream_t (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous: they return once the work is
+ *     enqueued; lp_sync() waits and returns a sticky device error (e.g. LP_ETIMEOUT).
+ *     Entry points named *_host take host pointers and are synchronous.
+ *   - Ownership: the caller owns every input and output buffer; the library never frees
+ *     caller memory.  The context owns the device memory it allocates (keys in the
+ *     transform domain, scratch) and frees it in lp_destroy.
+ *   - Outputs may not alias inputs.  Calls on one context must be issued from one host
+ *     thread at a time and on one stream at a time (they share the context's scratch).
+ *   - Return value: LP_OK (0) or a negative LP_E* code; lp_last_error() gives a
+ *     thread-local message for the last failure.  Nothing throws across this ABI.
+ */
+#ifndef LOCPIR_H
+#define LOCPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define LP_OK 0
+#define LP_EINVAL (-1)   /* bad argument: size, null pointer, unsupported parameter   */
+#define LP_ENOMEM (-2)   /* device allocation failed                                    */
+#define LP_ECUDA (-3)    /* a CUDA runtime call failed                                  */
+#define LP_ENOKEY (-4)   /* an evaluation was requested before both keys were loaded    */
+#define LP_ETIMEOUT (-5) /* a device-side wait gave up (bounded waits, ~2 s)            */
+#define LP_EBUSY (-6)    /* the server's memory budget is exhausted                     */
+#define LP_ECORRUPT (-7) /* key data failed its checksum                                */
+
+/* ---- parameters ---------------------------------------------------------------------
+ * TFHE parameters: LWE dimension n, ring degree N, TRLWE dimension k, gadget base 2^Bgbit
+ * with lg levels, key-switch base 2^basebit with t digits.  The paper fixes n (Section 5,
+ * TFHE Parameters: 630 for the 128-bit set, 540 for the 80-bit set) and defers the rest to
+ * TFHE; this build supports N = 1024, k = 1, Bgbit = 10, lg = 3, basebit = 2, t = 8 and
+ * any n in [1, 1023]. */
+typedef struct lp_params {
+    int n, N, k, Bgbit, lg, basebit, t;
+} lp_params;
+
+/* Gate identifiers.  HomAND is Bootstrap((0, -1/8) + c1 + c2) (Section 2.2, EvalGate); the
+ * other gates are the TFHE gate constructions the paper refers to (Section 2.2): NAND
+ * (0, 1/8) - c1 - c2, OR (0, 1/8) + c1 + c2, XOR (0, 1/4) + 2c1 + 2c2, XNOR
+ * (0, -1/4) - 2c1 - 2c2, NOT = -c1 (no bootstrap), MUX(a, b, c) = a ? b : c from two
+ * blind rotations of (0, -1/8) + a + b and (0, -1/8) - a + c summed with (0, 1/8) in
+ * dimension N and one key switch. */
+enum lp_op { LP_NAND = 0, LP_AND = 1, LP_OR = 2, LP_XOR = 3, LP_XNOR = 4, LP_NOT = 5, LP_MUX = 6 };
+
+/* Comparator kinds: LP_LT = HomCompS(x1, x2) (Algorithm 2, x1 < x2); LP_LE = HomCompLE(x1,
+ * x2) = NOT HomCompS(x2, x1) (x1 <= x2; Section 4.2 defines HomCompLE as the negation of
+ * HomCompS, read with swapped operands so that it is the inclusive bound Algorithm 3 uses). */
+enum lp_cmp { LP_LT = 0, LP_LE = 1 };
+
+/* Combination of the per-box services (Algorithm 3, last line; Algorithm 4).
+ * LP_XOR_TREE: pairwise XOR over boxes level by level (box 2i with 2i+1, an odd last row
+ * carried up); LP_XOR_CHAIN: Algorithm 4 as printed, S = Enc(0)^m then S[j] ^= S_i[j] box by
+ * box; LP_OR_TREE: the tree with OR (correct also for overlapping boxes). */
+enum lp_combine { LP_XOR_TREE = 0, LP_XOR_CHAIN = 1, LP_OR_TREE = 2 };
+
+typedef struct lp_ctx lp_ctx;
+
+/* Fill *p with n = 630, N = 1024, k = 1, Bgbit = 10, lg = 3, basebit = 2, t = 8. */
+int lp_params_default(lp_params *p);
+
+/* Create a context on CUDA device `device`.  Fails with LP_EINVAL for unsupported
+ * parameters, LP_ECUDA if the device cannot be used. */
+int lp_create(const lp_params *p, int device, lp_ctx **out);
+int lp_destroy(lp_ctx *ctx);
+
+/* Wait for all work the context enqueued; returns LP_ETIMEOUT if a device wait gave up
+ * since the last lp_sync (the flag is then cleared), LP_ECUDA on a CUDA error. */
+int lp_sync(lp_ctx *ctx);
+
+const char *lp_strerror(int code);
+const char *lp_last_error(void);
+
+/* ---- keys (KeyGen, Section 2.2: PK = {bootstrapping key, key-switching key}) ----------
+ * Bootstrapping key, coefficient domain, layout [n][2 lg][2][N] uint32 (words =
+ * n * 2 lg * 2 * N): row r = c lg + p of BSK_i is a TRLWE sample (component 0 = mask,
+ * 1 = body) with s_i 2^(32 - Bgbit (p+1)) added to coefficient 0 of component c.  The
+ * library converts it to its transform domain (two NTT primes) on the device and keeps
+ * only that copy.  LP_EINVAL if words does not match. */
+int lp_load_bsk(lp_ctx *ctx, const uint32_t *bsk, size_t words);
+int lp_load_bsk_device(lp_ctx *ctx, const uint32_t *bsk_dev, size_t words, void *stream);
+
+/* Key-switching key, layout [N][t][2^basebit][n + 1] uint32: entry [i][j][v] is an LWE
+ * sample of v S_i 2^(32 - basebit (j+1)) under s.  Entries with v = 0 are never read. */
+int lp_load_ksk(lp_ctx *ctx, const uint32_t *ksk, size_t words);
+int lp_load_ksk_device(lp_ctx *ctx, const uint32_t *ksk_dev, size_t words, void *stream);
+
+/* ---- gate bootstrapping ----------------------------------------------------------------
+ * lp_gate_batch: count independent gates out[g] = op(a[g], b[g]) (MUX: a[g] ? b[g] : c[g];
+ * NOT reads a only; c is read by MUX only and may be NULL otherwise).  All pointers device,
+ * [count][n + 1].  Each bootstrapped gate is: linear pre-combination, modulus switch to
+ * Z_2N, blind rotation (n CMux external products with the bootstrapping key), sample
+ * extraction, key switch.  LP_ENOKEY before both keys are loaded.  count = 0 is a no-op. */
+int lp_gate_batch(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                  uint32_t *out, size_t count, void *stream);
+
+/* Same, host pointers; copies in and out and synchronises. */
+int lp_gate_batch_host(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                       uint32_t *out, size_t count);
+
+/* The two halves of a bootstrap, exposed for step-level parity checks.
+ * lp_bootstrap_extract: count LWEs [count][n + 1] -> modulus switch, blind rotation with
+ * test vector v_j = mu for all j, sample extraction -> [count][N + 1] N-LWEs under S.
+ * lp_key_switch: count N-LWEs [count][N + 1] -> [count][n + 1] LWEs under s. */
+int lp_bootstrap_extract(lp_ctx *ctx, const uint32_t *lwe, uint32_t mu, uint32_t *ext, size_t count,
+                         void *stream);
+int lp_key_switch(lp_ctx *ctx, const uint32_t *ext, uint32_t *out, size_t count, void *stream);
+
+/* ---- circuits ---------------------------------------------------------------------------
+ * lp_compare_batch: count comparisons of l-bit values, x1 and x2 [count][l][n + 1] (LSB
+ * first), out [count][n + 1] encrypting x1 < x2 (LP_LT) or x1 <= x2 (LP_LE); is_signed
+ * selects two's-complement order (Algorithm 2 with its MSB flip) or unsigned order (the
+ * same loop without the flip).  Gates of all comparisons run in shared batches, level by
+ * level: l + 1 bootstrap levels. */
+int lp_compare_batch(lp_ctx *ctx, int kind, int is_signed, int l, const uint32_t *x1, const uint32_t *x2,
+                     uint32_t *out, size_t count, void *stream);
+
+/* One LocPIR query (Algorithm 3): point x, y [l][n + 1] each, n_boxes boxes
+ * [n_boxes][4][l][n + 1], services [n_boxes][m][n + 1]; out_service [m][n + 1] encrypts the
+ * combination (comb) of the services of the boxes that contain the point. */
+int lp_locpir_query(lp_ctx *ctx, int l, int is_signed, const uint32_t *x, const uint32_t *y, int n_boxes,
+                    const uint32_t *boxes, int m, const uint32_t *services, int comb, uint32_t *out_service,
+                    void *stream);
+
+/* Several LocPIR queries with their own l, n_boxes, m and pointers (uneven shapes); all
+ * their gates are scheduled together by bootstrap level.  Pointers as in lp_locpir_query. */
+typedef struct lp_query {
+    int l, is_signed, n_boxes, m, comb;
+    const uint32_t *x, *y, *boxes, *services;
+    uint32_t *out_service;
+} lp_query;
+int lp_locpir_batch(lp_ctx *ctx, const lp_query *q, size_t nq, void *stream);
+
+/* ---- client-side helpers on the device (no context) -------------------------------------
+ * Encrypt (Section 2.2) and the zero-phase samples of Algorithm 1: out[g] = (a_g,
+ * <a_g, s> + e_g + mu_g) with the caller's uniform masks mask [count][n], noise [count]
+ * and messages mu [count] (torus32).  s: [n] uint8 key bits.  Device pointers. */
+int lp_client_lwe_encrypt(int n, const uint8_t *s, const uint32_t *mask, const uint32_t *noise,
+                          const uint32_t *mu, uint32_t *out, size_t count, void *stream);
+/* phase[g] = b_g - <a_g, s> (Decrypt rounds it: bit = (int32)phase > 0). */
+int lp_client_lwe_phase(int n, const uint8_t *s, const uint32_t *ct, uint32_t *phase, size_t count,
+                        void *stream);
+/* Bootstrapping key from its randomness: S [N] key bits, mask and noise [n][2 lg][N];
+ * row r = c lg + p is (a, a S + e) with s_i 2^(32 - Bgbit (p+1)) added to coefficient 0 of
+ * component c.  Output [n][2 lg][2][N].  Device pointers. */
+int lp_client_keygen_bsk(const lp_params *p, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                         const uint32_t *noise, uint32_t *bsk, void *stream);
+/* Key-switching key: mask [N][t][2^basebit][n], noise [N][t][2^basebit]; output
+ * [N][t][2^basebit][n + 1], entry [i][j][v] = (a, <a, s> + e + v S_i 2^(32 - basebit (j+1))). */
+int lp_client_keygen_ksk(const lp_params *p, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                         const uint32_t *noise, uint32_t *ksk, void *stream);
+
+/* ---- introspection -------------------------------------------------------------------- */
+/* Kernel launches this context has issued since creation (every launch of the library's
+ * own kernels counts one). */
+uint64_t lp_launch_count(const lp_ctx *ctx);
+/* Average device time (ms) of the blind-rotation kernel over the launches timed since the
+ * last reset, measured with CUDA events on the launching stream; *launches receives the
+ * number of timed launches.  Timing is enabled by lp_set_timing(ctx, 1). */
+int lp_set_timing(lp_ctx *ctx, int enable);
+int lp_kernel_time(lp_ctx *ctx, const char *kernel, double *ms_total, uint64_t *launches);
+int lp_reset_timing(lp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOCPIR_H */

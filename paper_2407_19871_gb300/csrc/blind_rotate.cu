@@ -1,0 +1,401 @@
+// Blind rotation + sample extraction (the hot loop of gate bootstrapping) and the
+// conversion of the bootstrapping key to the transform domain.
+//
+// TFHE gate bootstrapping (Chillotti et al., J. Cryptology 2020; LocPIR Section 2.2
+// defers to it): ACC = (0, X^-bbar v); for i < n: ACC += BSK_i [x] ((X^abar_i - 1) ACC);
+// then extract coefficient 0 as an N-LWE.  Every ciphertext of a batch reads the same
+// BSK_i at step i, so one CTA runs BR_SLOTS ciphertexts in lock step and streams each
+// BSK_i slice from L2 into shared memory once for all of them.
+//
+// CTA layout (BR_THREADS = 8 warps, two per SM sub-partition so that each thread may
+// hold up to 255 registers):
+//   Warp w serves ciphertext slot w / 2 and NTT prime w % 2; the two warps of a slot (a
+//   "pair") split the external product by prime and meet twice per step (named barrier
+//   1 + slot, 64 threads).
+//   Key chunks (one chunk = row r of BSK_i for one prime, both TRLWE components, 8 KB)
+//   flow through a ring of BR_RING shared-memory slots per prime.  Lane 0 of the slot-0
+//   warp of each prime is also that prime's producer: it issues cp.async.bulk copies
+//   (TMA engine) completing on "full" mbarriers, refilling the slot released one chunk
+//   earlier (all BR_SLOTS consumers arrive on its "empty" mbarrier), i.e. BR_RING - 1
+//   chunks ahead.  All waits are bounded (LP_ETIMEOUT on expiry).
+//
+// Per step and pair: both warps rotate/subtract ACC (shared memory) and decompose it;
+// each warp forward-transforms the 6 digit polynomials modulo its prime, multiplies them
+// with the key chunk (Montgomery, key stored as NTT(b) N^-1 2^32 mod p) accumulating both
+// output components, inverse-transforms the 2 sums; the prime-0 warp hands its residues
+// over shared memory; the prime-1 warp recombines them (centred CRT) and adds to ACC.
+#include "common.cuh"
+#include "kernels.h"
+#include "ntt.cuh"
+
+namespace lp {
+
+constexpr int BR_SLOTS = 4;
+constexpr int BR_RING = 4;
+constexpr int BR_COMPUTE_WARPS = 2 * BR_SLOTS;
+constexpr int BR_THREADS = BR_COMPUTE_WARPS * 32;
+constexpr int CHUNK_WORDS = 2 * RING_N;                 // one (i, prime, row) chunk
+constexpr uint32_t CHUNK_BYTES = CHUNK_WORDS * 4u;
+constexpr int ABAR_STRIDE_MAX = 1024;                    // u16 entries per job (>= n + 1)
+
+struct __align__(16) BrSmem {
+    uint32_t ring[2][BR_RING][CHUNK_WORDS];              // 64 KB
+    uint32_t acc[BR_SLOTS][2][RING_N];                   // 32 KB
+    uint32_t xch[BR_SLOTS][2][RING_N];                   // 32 KB
+    uint32_t tbuf[BR_COMPUTE_WARPS][32 * 33];            // 33 KB
+    uint2 tw[2][2][LANE_TW * 32];                        // 31 KB [prime][dir]
+    uint16_t abar[BR_SLOTS][ABAR_STRIDE_MAX];            // 8 KB
+    uint64_t full_bar[2][BR_RING];
+    uint64_t empty_bar[2][BR_RING];
+    int abort;
+};
+
+struct BrArgs {
+    const uint16_t *abar;      // [jobs][abar_stride]: abar_0 .. abar_{n-1}, bbar at index n
+    uint32_t *ext;             // [jobs][EXT_STRIDE]: extracted a'_0 .. a'_{N-1}, b' at index N
+    const uint32_t *bsk_hat;   // [n][2 primes][ROWS][2][N] (transform domain, chunk layout)
+    const uint2 *tw_lane;      // [2][2][LANE_TW * 32]
+    int n;
+    int abar_stride;
+    int jobs;
+    uint32_t mu;               // test-vector value (1/8)
+    int *err;
+};
+
+size_t br_smem_bytes() { return sizeof(BrSmem); }
+
+// Chunk stream of one prime: chunk q of a CTA is row q % ROWS of BSK_((q / ROWS) % n),
+// for q < total (= the CTA's groups * n * ROWS).
+struct Producer {
+    const uint32_t *bsk_hat;
+    uint32_t total;
+    uint32_t issued;
+    int n;
+};
+
+template <int PI>
+__device__ __forceinline__ void produce(BrSmem &sm, Producer &pr, uint32_t upto)
+{
+    // Issue chunks [pr.issued, min(upto, total)) into their ring slots; slot of chunk q
+    // is free once chunk q - BR_RING was released by all consumers.
+    while (pr.issued < upto && pr.issued < pr.total) {
+        const uint32_t q = pr.issued;
+        const uint32_t s = q % BR_RING;
+        if (q >= (uint32_t)BR_RING) {
+            const uint32_t par = ((q - BR_RING) / BR_RING) & 1u;
+            if (!mbar_wait_bounded(&sm.empty_bar[PI][s], par, &sm.abort)) {
+                *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+                return;
+            }
+        }
+        const int r = (int)(q % ROWS);
+        const int i = (int)((q / ROWS) % (uint32_t)pr.n);
+        mbar_arrive_expect_tx(&sm.full_bar[PI][s], CHUNK_BYTES);
+        const uint32_t *src = pr.bsk_hat + ((size_t)(i * 2 + PI) * ROWS + r) * CHUNK_WORDS;
+        bulk_copy_g2s(sm.ring[PI][s], src, CHUNK_BYTES, &sm.full_bar[PI][s]);
+        pr.issued++;
+    }
+}
+
+// Wait (bounded) until every chunk issued by this producer has landed in shared memory.
+template <int PI>
+__device__ __forceinline__ bool drain(BrSmem &sm, const Producer &pr)
+{
+    bool ok = true;
+    const uint32_t first = pr.issued > (uint32_t)BR_RING ? pr.issued - BR_RING : 0u;
+    volatile int never = 0;
+    for (uint32_t q = first; q < pr.issued; q++)
+        ok &= mbar_wait_bounded(&sm.full_bar[PI][q % BR_RING], (q / BR_RING) & 1u, &never);
+    return ok;
+}
+
+// One external-product half for prime PI: rotate/decompose ACC, 6 forward NTTs each
+// followed by the multiply-accumulate with the streamed key chunk, 2 inverse NTTs.
+// On return acc0 / acc1 hold the two output components mod p in [0, p), layout A.
+template <int PI>
+__device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane, int ab, bool work,
+                                                 uint32_t &cseq, uint32_t (&acc0)[32], uint32_t (&acc1)[32],
+                                                 uint32_t *tbuf, Producer &pr, bool producer)
+{
+    constexpr uint32_t P = Prime<PI>::p;
+    const uint32_t pinv = c_pinv_neg[PI];
+    const uint2 *twf = sm.tw[PI][0];
+    const uint2 *twi = sm.tw[PI][1];
+    bool ok = true;
+    uint32_t u[32];
+    uint32_t x[32];
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        acc0[k] = 0u;
+        acc1[k] = 0u;
+    }
+#pragma unroll 1
+    for (int c = 0; c < 2; c++) {
+        if (work) {
+            const uint32_t *A = sm.acc[slot][c];
+#pragma unroll
+            for (int k = 0; k < 32; k++) {
+                const int j = lane + 32 * k;
+                const int idx = (j - ab) & (2 * RING_N - 1);
+                uint32_t v = A[idx & (RING_N - 1)];
+                v = (idx & RING_N) ? (0u - v) : v;
+                u[k] = v - A[j] + GADGET_OFF;
+            }
+        }
+#pragma unroll 1
+        for (int p = 0; p < LG; p++) {
+            const int sh = 22 - BGBIT * p;
+            if (work) {
+#pragma unroll
+                for (int k = 0; k < 32; k++) x[k] = ((u[k] >> sh) & 1023u) + (P - 512u);
+                ntt_fwd<PI>(x, tbuf, twf, lane);
+            }
+            const uint32_t rs = cseq % BR_RING;
+            const uint32_t par = (cseq / BR_RING) & 1u;
+            if (ok && !mbar_wait_bounded(&sm.full_bar[PI][rs], par, &sm.abort)) {
+                ok = false;
+                if (lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+            }
+            if (work && ok) {
+                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[PI][rs]);
+                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[PI][rs] + RING_N);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const uint4 b0 = ch0[q * 32 + lane];
+                    const uint4 b1 = ch1[q * 32 + lane];
+                    const uint32_t bb0[4] = {b0.x, b0.y, b0.z, b0.w};
+                    const uint32_t bb1[4] = {b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int k = 4 * q + e;
+                        uint32_t t0 = acc0[k] + mont_mul<P>(x[k], bb0[e], pinv);
+                        acc0[k] = umin_u32(t0, t0 - 2u * P);
+                        uint32_t t1 = acc1[k] + mont_mul<P>(x[k], bb1[e], pinv);
+                        acc1[k] = umin_u32(t1, t1 - 2u * P);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sm.empty_bar[PI][rs]);
+                // Refill the slot released one chunk ago (BR_RING - 1 chunks of lookahead).
+                if (producer) produce<PI>(sm, pr, cseq + BR_RING);
+            }
+            __syncwarp();
+            cseq++;
+        }
+    }
+    if (work && ok) {
+        ntt_inv<PI>(acc0, tbuf, twi, lane);
+        ntt_inv<PI>(acc1, tbuf, twi, lane);
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            acc0[k] = umin_u32(acc0[k], acc0[k] - P);
+            acc1[k] = umin_u32(acc1[k], acc1[k] - P);
+        }
+    }
+    return ok;
+}
+
+__device__ __forceinline__ uint32_t crt_lift(uint32_t x0, uint32_t x1)
+{
+    // V = x0 + p0 t, t = (x1 - x0) p0^-1 mod p1, V in [0, p0 p1); centred lift mod 2^32.
+    constexpr uint64_t PP = (uint64_t)PRIME0 * (uint64_t)PRIME1;
+    const uint2 inv = c_crt;
+    uint32_t x0r = umin_u32(x0, x0 - PRIME1);
+    uint32_t d = x1 - x0r + PRIME1;
+    uint32_t t = shoup_mul<PRIME1>(d, inv.x, inv.y);
+    t = umin_u32(t, t - PRIME1);
+    const uint64_t V = (uint64_t)PRIME0 * t + x0;
+    uint32_t r = (uint32_t)V;
+    if (V > (PP - 1) / 2) r -= (uint32_t)PP;
+    return r;
+}
+
+// Loop of one compute warp (prime PI) over its CTA's ciphertext groups.
+template <int PI>
+__device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int warp, int lane, int ngroups)
+{
+    const int slot = warp >> 1;
+    const int bar_id = 1 + slot;
+    const int n = a.n;
+    uint32_t *tbuf = sm.tbuf[warp];
+    uint32_t cseq = 0;
+    uint32_t acc0[32], acc1[32];
+    const bool producer = slot == 0 && lane == 0;
+    Producer pr;
+    pr.bsk_hat = a.bsk_hat;
+    pr.n = n;
+    pr.issued = 0;
+    const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    pr.total = (uint32_t)my_groups * (uint32_t)n * ROWS;
+    if (producer) produce<PI>(sm, pr, BR_RING);
+
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int job = g * BR_SLOTS + slot;
+        const bool active = job < a.jobs;
+        if (PI == 1 && active) {
+            const uint16_t *src = a.abar + (size_t)job * a.abar_stride;
+            for (int i = lane; i <= n; i += 32) sm.abar[slot][i] = src[i];
+            __syncwarp();
+            const int bb = sm.abar[slot][n];
+            // ACC = (0, X^-bbar v): coefficient j of X^-k v is v (j + k < N) or -v.
+            for (int j = lane; j < RING_N; j += 32) {
+                sm.acc[slot][0][j] = 0u;
+                const int e = (j + bb) & (2 * RING_N - 1);
+                sm.acc[slot][1][j] = (e & RING_N) ? (0u - a.mu) : a.mu;
+            }
+        }
+        bool aborted = bar_red_or(bar_id, 64, false);
+        for (int i = 0; i < n && !aborted; i++) {
+            const int ab = active ? (int)sm.abar[slot][i] : 0;
+            const bool work = ab != 0;
+            const bool ok = external_product<PI>(sm, slot, lane, ab, work, cseq, acc0, acc1, tbuf, pr, producer);
+            if (PI == 0 && work && ok) {
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    sm.xch[slot][0][lane + 32 * k] = acc0[k];
+                    sm.xch[slot][1][lane + 32 * k] = acc1[k];
+                }
+            }
+            aborted = bar_red_or(bar_id, 64, !ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
+            if (aborted) break;
+            if (PI == 1 && work) {
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    const int j = lane + 32 * k;
+                    sm.acc[slot][0][j] += crt_lift(sm.xch[slot][0][j], acc0[k]);
+                    sm.acc[slot][1][j] += crt_lift(sm.xch[slot][1][j], acc1[k]);
+                }
+            }
+            aborted = bar_red_or(bar_id, 64, false);
+        }
+        if (aborted) {
+            if (lane == 0 && PI == 1) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            break;
+        }
+        if (PI == 1 && active) {
+            // Sample extraction: a'_0 = A_0, a'_j = -A_{N-j}, b' = B_0.
+            uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
+            for (int j = lane; j < RING_N; j += 32)
+                dst[j] = j == 0 ? sm.acc[slot][0][0] : 0u - sm.acc[slot][0][RING_N - j];
+            if (lane == 0) dst[RING_N] = sm.acc[slot][1][0];
+        }
+    }
+    // No bulk copy may still be in flight when the CTA exits.
+    if (producer && !drain<PI>(sm, pr)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BrSmem &sm = *reinterpret_cast<BrSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    for (int i = threadIdx.x; i < 2 * 2 * LANE_TW * 32; i += blockDim.x) (&sm.tw[0][0][0])[i] = a.tw_lane[i];
+    if (threadIdx.x == 0) {
+        for (int p = 0; p < 2; p++)
+            for (int s = 0; s < BR_RING; s++) {
+                mbar_init(&sm.full_bar[p][s], 1);
+                mbar_init(&sm.empty_bar[p][s], BR_SLOTS);
+            }
+        sm.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int ngroups = (a.jobs + BR_SLOTS - 1) / BR_SLOTS;
+
+    // ---------------- compute warps ----------------
+    if ((warp & 1) == 0) compute_warp<0>(sm, a, warp, lane, ngroups);
+    else compute_warp<1>(sm, a, warp, lane, ngroups);
+}
+
+// ---------------------------------------------------------------------------------
+// Bootstrapping key -> transform domain.  One warp per (i, prime, row, component)
+// polynomial: centred lift mod p, forward NTT, scale by N^-1 2^32 mod p, store in the
+// chunk layout the blind rotation reads (component c, then [q][lane][4] so that lane t
+// finds registers k = 4q .. 4q+3 of layout B in one 16-byte load).
+// ---------------------------------------------------------------------------------
+struct ConvSmem {
+    uint32_t tbuf[8][32 * 33];
+    uint2 tw[2][LANE_TW * 32];   // forward tables of both primes
+};
+
+__global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, uint32_t *bsk_hat, int n,
+                                                         const uint2 *tw_lane, uint2 scale0, uint2 scale1)
+{
+    __shared__ ConvSmem sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < LANE_TW * 32; i += blockDim.x) {
+        sm.tw[0][i] = tw_lane[(0 * 2 + 0) * LANE_TW * 32 + i];
+        sm.tw[1][i] = tw_lane[(1 * 2 + 0) * LANE_TW * 32 + i];
+    }
+    __syncthreads();
+    const long total = (long)n * 2 * ROWS * 2;
+    for (long poly = (long)blockIdx.x * 8 + warp; poly < total; poly += (long)gridDim.x * 8) {
+        const int c = (int)(poly % 2);
+        const int r = (int)((poly / 2) % ROWS);
+        const int p = (int)((poly / (2 * ROWS)) % 2);
+        const long i = poly / (4 * ROWS);
+        const uint32_t *src = bsk + ((i * ROWS + r) * 2 + c) * RING_N;
+        const uint32_t P = p == 0 ? PRIME0 : PRIME1;
+        uint32_t x[32];
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const int32_t v = (int32_t)src[lane + 32 * k];
+            int64_t m = (int64_t)v % (int64_t)P;
+            if (m < 0) m += P;
+            x[k] = (uint32_t)m;
+        }
+        if (p == 0) ntt_fwd<0>(x, sm.tbuf[warp], sm.tw[0], lane);
+        else ntt_fwd<1>(x, sm.tbuf[warp], sm.tw[1], lane);
+        const uint2 sc = p == 0 ? scale0 : scale1;   // (N^-1 2^32 mod p, unused)
+        uint32_t *dst = bsk_hat + ((i * 2 + p) * ROWS + r) * CHUNK_WORDS + c * RING_N;
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const uint64_t y = (uint64_t)(x[k] % P) * sc.x % P;
+            dst[(k >> 2) * 128 + lane * 4 + (k & 3)] = (uint32_t)y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------------
+cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                      const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
+                      cudaStream_t st)
+{
+    if (jobs <= 0) return cudaSuccess;
+    const size_t smem = sizeof(BrSmem);
+    cudaError_t e = cudaFuncSetAttribute(br_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
+    const int groups = (jobs + BR_SLOTS - 1) / BR_SLOTS;
+    const int grid = groups < num_sms ? groups : num_sms;
+    br_kernel<<<grid, BR_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t upload_constants(const NttTables &t)
+{
+    cudaError_t e = cudaMemcpyToSymbol(c_tw, t.ctw, sizeof(t.ctw));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pinv_neg, t.pinv_neg, sizeof(t.pinv_neg));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_crt, &t.crt, sizeof(t.crt));
+    return e;
+}
+
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane,
+                              uint32_t scale0, uint32_t scale1, int num_sms, cudaStream_t st)
+{
+    const long polys = (long)n * 2 * ROWS * 2;
+    long grid = (polys + 7) / 8;
+    if (grid > 4L * num_sms) grid = 4L * num_sms;
+    bsk_to_ntt_kernel<<<(int)grid, 256, 0, st>>>(bsk, bsk_hat, n, tw_lane, make_uint2(scale0, 0),
+                                                 make_uint2(scale1, 0));
+    return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -1,0 +1,419 @@
+// Gate pre-combination + modulus switch, batched key switching, and the client-side
+// kernels (encryption, phase, key generation from given randomness).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lp {
+
+// ---------------------------------------------------------------------------------
+// Pre-combination + modulus switch.
+// A bootstrapped gate first forms the linear combination (0, const) + sum_k coef_k c_k
+// (LocPIR Section 2.2, EvalGate: HomAND uses (0, -1/8) + c1 + c2), then rounds every
+// coefficient to Z_2N: abar = ((x + 2^20) mod 2^32) >> 21 (half up).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint16_t modswitch_2048(uint32_t x) { return (uint16_t)((x + (1u << 20)) >> 21); }
+
+__device__ __forceinline__ void gate_coefs(int op, int half, uint32_t &cst, int &ca, int &cb, int &cc)
+{
+    cc = 0;
+    switch (op) {
+    case LP_AND: cst = 0u - T_EIGHTH; ca = 1; cb = 1; break;
+    case LP_NAND: cst = T_EIGHTH; ca = -1; cb = -1; break;
+    case LP_OR: cst = T_EIGHTH; ca = 1; cb = 1; break;
+    case LP_XOR: cst = T_QUARTER; ca = 2; cb = 2; break;
+    case LP_XNOR: cst = 0u - T_QUARTER; ca = -2; cb = -2; break;
+    default:  // MUX: half 0 = (0,-1/8) + a + b, half 1 = (0,-1/8) - a + c
+        cst = 0u - T_EIGHTH;
+        if (half == 0) { ca = 1; cb = 1; }
+        else { ca = -1; cb = 0; cc = 1; }
+        break;
+    }
+}
+
+// Dense gate batch: job jb < count * halves; gate g = jb % count, half = jb / count.
+__global__ void precomb_dense_kernel(int op, const uint32_t *a, const uint32_t *b, const uint32_t *c, int n,
+                                     size_t count, size_t jobs, uint16_t *abar, int abar_stride)
+{
+    const size_t total = jobs * (size_t)(n + 1);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t jb = idx / (n + 1);
+        const int w = (int)(idx % (n + 1));
+        const size_t g = jb % count;
+        const int half = (int)(jb / count);
+        uint32_t cst; int ca, cb, cc;
+        gate_coefs(op, half, cst, ca, cb, cc);
+        const size_t off = g * (size_t)(n + 1) + w;
+        uint32_t x = (uint32_t)ca * a[off];
+        if (cb) x += (uint32_t)cb * b[off];
+        if (cc) x += (uint32_t)cc * c[off];
+        if (w == n) x += cst;
+        abar[jb * abar_stride + w] = modswitch_2048(x);
+    }
+}
+
+// Plain modulus switch of given LWEs (lp_bootstrap_extract).
+__global__ void modswitch_kernel(const uint32_t *lwe, int n, size_t jobs, uint16_t *abar, int abar_stride)
+{
+    const size_t total = jobs * (size_t)(n + 1);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t jb = idx / (n + 1);
+        const int w = (int)(idx % (n + 1));
+        abar[jb * abar_stride + w] = modswitch_2048(lwe[idx]);
+    }
+}
+
+// Circuit mode: job records index a ciphertext pool [slots][n + 1].
+__global__ void precomb_indexed_kernel(const BrJob *jobs, size_t njobs, const uint32_t *pool, int n,
+                                       uint16_t *abar, int abar_stride)
+{
+    const size_t total = njobs * (size_t)(n + 1);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t jb = idx / (n + 1);
+        const int w = (int)(idx % (n + 1));
+        const BrJob J = jobs[jb];
+        uint32_t x = 0u;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            if (J.coef[k] != 0) x += (uint32_t)J.coef[k] * pool[(size_t)J.in[k] * (n + 1) + w];
+        if (w == n) x += J.bconst;
+        abar[jb * abar_stride + w] = modswitch_2048(x);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Key switching.  For an N-LWE (a', b'): out = (0, b') - sum_{i<N, j<t} KSK[i][j][v_ij],
+// v_ij = ((a'_i + 2^15) >> (30 - 2j)) & 3, skipping v = 0.  A CTA takes KS_CT outputs
+// and all n + 1 output words (KS_COLS per thread); every KSK row it reads serves KS_CT
+// ciphertexts.  MUX jobs sum their two extracted samples and (0, 1/8) while staging.
+// ---------------------------------------------------------------------------------
+constexpr int KS_CT = 16;
+constexpr int KS_THREADS = 128;
+constexpr int KS_COLS = 5;      // n + 1 <= 640
+constexpr int KS_ICHUNK = 64;
+
+__global__ void __launch_bounds__(KS_THREADS) ks_kernel(const uint32_t *ext, const KsJob *jobs, size_t njobs,
+                                                        int dense_mux, uint32_t *out, const uint32_t *ksk, int n)
+{
+    __shared__ uint32_t xs[KS_CT][KS_ICHUNK];
+    __shared__ uint32_t body[KS_CT];
+    __shared__ int srcs[KS_CT][2];
+    __shared__ int dsts[KS_CT];
+    const int tid = threadIdx.x;
+    const size_t first = (size_t)blockIdx.x * KS_CT;
+    if (tid < KS_CT) {
+        const size_t g = first + tid;
+        int e1 = -1, e2 = -1, o = -1;
+        uint32_t bc = 0u;
+        if (g < njobs) {
+            if (jobs) {
+                const KsJob J = jobs[g];
+                e1 = J.e1; e2 = J.e2; bc = J.bconst; o = J.out;
+            } else {
+                e1 = (int)g; o = (int)g;
+                if (dense_mux) { e2 = (int)(g + njobs); bc = T_EIGHTH; }
+            }
+            uint32_t bsum = ext[(size_t)e1 * EXT_STRIDE + RING_N] + bc;
+            if (e2 >= 0) bsum += ext[(size_t)e2 * EXT_STRIDE + RING_N];
+            body[tid] = bsum;
+        } else {
+            body[tid] = 0u;
+        }
+        srcs[tid][0] = e1; srcs[tid][1] = e2; dsts[tid] = o;
+    }
+    __syncthreads();
+
+    const int W = n + 1;
+    uint32_t acc[KS_CT][KS_COLS];
+#pragma unroll
+    for (int ct = 0; ct < KS_CT; ct++)
+#pragma unroll
+        for (int q = 0; q < KS_COLS; q++) acc[ct][q] = (tid + KS_THREADS * q == n) ? body[ct] : 0u;
+
+    for (int i0 = 0; i0 < RING_N; i0 += KS_ICHUNK) {
+        __syncthreads();
+        for (int e = tid; e < KS_CT * KS_ICHUNK; e += KS_THREADS) {
+            const int ct = e / KS_ICHUNK, ii = e % KS_ICHUNK;
+            const int e1 = srcs[ct][0], e2 = srcs[ct][1];
+            uint32_t v = 0u;
+            if (e1 >= 0) {
+                v = ext[(size_t)e1 * EXT_STRIDE + i0 + ii];
+                if (e2 >= 0) v += ext[(size_t)e2 * EXT_STRIDE + i0 + ii];
+            }
+            xs[ct][ii] = v + (1u << 15);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int ii = 0; ii < KS_ICHUNK; ii++) {
+            const int i = i0 + ii;
+            uint32_t xv[KS_CT];
+#pragma unroll
+            for (int ct = 0; ct < KS_CT; ct++) xv[ct] = xs[ct][ii];
+#pragma unroll 2
+            for (int j = 0; j < KS_T; j++) {
+                const uint32_t *row = ksk + (size_t)((i * KS_T + j) * KS_BASE) * W;
+                uint32_t k1[KS_COLS], k2[KS_COLS], k3[KS_COLS];
+#pragma unroll
+                for (int q = 0; q < KS_COLS; q++) {
+                    const int col = tid + KS_THREADS * q;
+                    const bool ok = col < W;
+                    k1[q] = ok ? __ldg(row + W + col) : 0u;
+                    k2[q] = ok ? __ldg(row + 2 * W + col) : 0u;
+                    k3[q] = ok ? __ldg(row + 3 * W + col) : 0u;
+                }
+                const int sh = 30 - 2 * j;
+#pragma unroll
+                for (int ct = 0; ct < KS_CT; ct++) {
+                    const uint32_t v = (xv[ct] >> sh) & 3u;
+#pragma unroll
+                    for (int q = 0; q < KS_COLS; q++) {
+                        uint32_t s = v == 1u ? k1[q] : 0u;
+                        s = v == 2u ? k2[q] : s;
+                        s = v == 3u ? k3[q] : s;
+                        acc[ct][q] -= s;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int ct = 0; ct < KS_CT; ct++) {
+        const int o = dsts[ct];
+        if (o < 0) continue;
+#pragma unroll
+        for (int q = 0; q < KS_COLS; q++) {
+            const int col = tid + KS_THREADS * q;
+            if (col < W) out[(size_t)o * W + col] = acc[ct][q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Small helpers: negated copy (NOT), trivial constants, pool gather with negation.
+// ---------------------------------------------------------------------------------
+__global__ void negate_kernel(const uint32_t *in, uint32_t *out, size_t words)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = 0u - in[i];
+}
+
+__global__ void gather_kernel(const uint32_t *pool, const int *slots, const uint8_t *neg, size_t cnt, int n,
+                              uint32_t *out)
+{
+    const size_t total = cnt * (size_t)(n + 1);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t g = idx / (n + 1);
+        const int w = (int)(idx % (n + 1));
+        const uint32_t v = pool[(size_t)slots[g] * (n + 1) + w];
+        out[idx] = neg[g] ? 0u - v : v;
+    }
+}
+
+__global__ void trivial_kernel(uint32_t *dst, int n, uint32_t b)
+{
+    for (int w = threadIdx.x; w <= n; w += blockDim.x) dst[w] = (w == n) ? b : 0u;
+}
+
+// ---------------------------------------------------------------------------------
+// Client side (device): Encrypt and phase, one warp per ciphertext; key generation.
+// ---------------------------------------------------------------------------------
+__global__ void lwe_encrypt_kernel(int n, const uint8_t *s, const uint32_t *mask, const uint32_t *noise,
+                                   const uint32_t *mu, uint32_t *out, size_t count)
+{
+    const size_t warps = (size_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (size_t g = (size_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); g < count; g += warps) {
+        const uint32_t *a = mask + g * (size_t)n;
+        uint32_t *c = out + g * (size_t)(n + 1);
+        uint32_t dot = 0u;
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t ai = a[i];
+            c[i] = ai;
+            dot += s[i] ? ai : 0u;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) c[n] = dot + noise[g] + mu[g];
+    }
+}
+
+__global__ void lwe_phase_kernel(int n, const uint8_t *s, const uint32_t *ct, uint32_t *phase, size_t count)
+{
+    const size_t warps = (size_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (size_t g = (size_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); g < count; g += warps) {
+        const uint32_t *c = ct + g * (size_t)(n + 1);
+        uint32_t dot = 0u;
+        for (int i = lane; i < n; i += 32) dot += s[i] ? c[i] : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) phase[g] = c[n] - dot;
+    }
+}
+
+// One CTA per TRGSW row (i, r): body = mask * S + noise (negacyclic, S binary), gadget
+// term s_i 2^(32 - Bgbit (p+1)) on coefficient 0 of component c = r / lg.
+__global__ void __launch_bounds__(256) keygen_bsk_kernel(int n, const uint8_t *s, const uint8_t *S,
+                                                         const uint32_t *mask, const uint32_t *noise,
+                                                         uint32_t *bsk)
+{
+    __shared__ uint32_t A[RING_N];
+    __shared__ uint8_t Sk[RING_N];
+    for (int j = threadIdx.x; j < RING_N; j += blockDim.x) Sk[j] = S[j];
+    for (long ir = blockIdx.x; ir < (long)n * ROWS; ir += gridDim.x) {
+        const int i = (int)(ir / ROWS), r = (int)(ir % ROWS);
+        __syncthreads();
+        for (int j = threadIdx.x; j < RING_N; j += blockDim.x) A[j] = mask[ir * RING_N + j];
+        __syncthreads();
+        uint32_t o[RING_N / 256];
+#pragma unroll
+        for (int q = 0; q < RING_N / 256; q++) o[q] = noise[ir * RING_N + threadIdx.x + 256 * q];
+        for (int k = 0; k < RING_N; k++) {
+            if (!Sk[k]) continue;
+#pragma unroll
+            for (int q = 0; q < RING_N / 256; q++) {
+                const int j = threadIdx.x + 256 * q;
+                const int d = j - k;
+                o[q] += d >= 0 ? A[d] : 0u - A[d + RING_N];
+            }
+        }
+        const int c = r / LG, p = r % LG;
+        const uint32_t g = s[i] ? (1u << (32 - BGBIT * (p + 1))) : 0u;
+        uint32_t *oa = bsk + (ir * 2 + 0) * RING_N;
+        uint32_t *ob = bsk + (ir * 2 + 1) * RING_N;
+#pragma unroll
+        for (int q = 0; q < RING_N / 256; q++) {
+            const int j = threadIdx.x + 256 * q;
+            oa[j] = A[j] + ((c == 0 && j == 0) ? g : 0u);
+            ob[j] = o[q] + ((c == 1 && j == 0) ? g : 0u);
+        }
+    }
+}
+
+__global__ void keygen_ksk_kernel(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                                  const uint32_t *noise, uint32_t *ksk)
+{
+    const size_t total = (size_t)RING_N * KS_T * KS_BASE;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (size_t e = (size_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); e < total; e += warps) {
+        const int i = (int)(e / (KS_T * KS_BASE));
+        const int j = (int)((e / KS_BASE) % KS_T);
+        const uint32_t v = (uint32_t)(e % KS_BASE);
+        const uint32_t *a = mask + e * (size_t)n;
+        uint32_t *c = ksk + e * (size_t)(n + 1);
+        uint32_t dot = 0u;
+        for (int w = lane; w < n; w += 32) {
+            const uint32_t aw = a[w];
+            c[w] = aw;
+            dot += s[w] ? aw : 0u;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) c[n] = dot + noise[e] + v * (uint32_t)S[i] * (1u << (32 - KS_BASEBIT * (j + 1)));
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------------
+static int grid_for(size_t work, int threads, int num_sms)
+{
+    size_t g = (work + threads - 1) / threads;
+    const size_t cap = (size_t)num_sms * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_precomb_dense(int op, const uint32_t *a, const uint32_t *b, const uint32_t *c, int n,
+                                 size_t count, uint16_t *abar, int abar_stride, int num_sms, cudaStream_t st)
+{
+    const size_t jobs = count * (op == LP_MUX ? 2 : 1);
+    precomb_dense_kernel<<<grid_for(jobs * (n + 1), 256, num_sms), 256, 0, st>>>(op, a, b, c, n, count, jobs,
+                                                                                  abar, abar_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modswitch(const uint32_t *lwe, int n, size_t jobs, uint16_t *abar, int abar_stride, int num_sms,
+                             cudaStream_t st)
+{
+    modswitch_kernel<<<grid_for(jobs * (n + 1), 256, num_sms), 256, 0, st>>>(lwe, n, jobs, abar, abar_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32_t *pool, int n, uint16_t *abar,
+                                   int abar_stride, int num_sms, cudaStream_t st)
+{
+    if (!njobs) return cudaSuccess;
+    precomb_indexed_kernel<<<grid_for(njobs * (n + 1), 256, num_sms), 256, 0, st>>>(jobs, njobs, pool, n, abar,
+                                                                                     abar_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
+                      const uint32_t *ksk, int n, cudaStream_t st)
+{
+    if (!njobs) return cudaSuccess;
+    const size_t grid = (njobs + KS_CT - 1) / KS_CT;
+    ks_kernel<<<(unsigned)grid, KS_THREADS, 0, st>>>(ext, jobs, njobs, dense_mux, out, ksk, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_negate(const uint32_t *in, uint32_t *out, size_t words, int num_sms, cudaStream_t st)
+{
+    if (!words) return cudaSuccess;
+    negate_kernel<<<grid_for(words, 256, num_sms), 256, 0, st>>>(in, out, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const uint32_t *pool, const int *slots, const uint8_t *neg, size_t cnt, int n,
+                          uint32_t *out, int num_sms, cudaStream_t st)
+{
+    if (!cnt) return cudaSuccess;
+    gather_kernel<<<grid_for(cnt * (n + 1), 256, num_sms), 256, 0, st>>>(pool, slots, neg, cnt, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trivial(uint32_t *dst, int n, uint32_t b, cudaStream_t st)
+{
+    trivial_kernel<<<1, 256, 0, st>>>(dst, n, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lwe_encrypt(int n, const uint8_t *s, const uint32_t *mask, const uint32_t *noise,
+                               const uint32_t *mu, uint32_t *out, size_t count, int num_sms, cudaStream_t st)
+{
+    if (!count) return cudaSuccess;
+    lwe_encrypt_kernel<<<grid_for(count * 32, 256, num_sms), 256, 0, st>>>(n, s, mask, noise, mu, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lwe_phase(int n, const uint8_t *s, const uint32_t *ct, uint32_t *phase, size_t count,
+                             int num_sms, cudaStream_t st)
+{
+    if (!count) return cudaSuccess;
+    lwe_phase_kernel<<<grid_for(count * 32, 256, num_sms), 256, 0, st>>>(n, s, ct, phase, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keygen_bsk(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                              const uint32_t *noise, uint32_t *bsk, int num_sms, cudaStream_t st)
+{
+    int grid = n * ROWS;
+    if (grid > num_sms * 8) grid = num_sms * 8;
+    keygen_bsk_kernel<<<grid, 256, 0, st>>>(n, s, S, mask, noise, bsk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keygen_ksk(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                              const uint32_t *noise, uint32_t *ksk, int num_sms, cudaStream_t st)
+{
+    const size_t total = (size_t)RING_N * KS_T * KS_BASE;
+    keygen_ksk_kernel<<<grid_for(total * 32, 256, num_sms), 256, 0, st>>>(n, s, S, mask, noise, ksk);
+    return cudaGetLastError();
+}
+
+}  // namespace lp

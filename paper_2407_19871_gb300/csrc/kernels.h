@@ -1,0 +1,62 @@
+// Internal launcher declarations of liblocpir (not part of the public C-ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lp {
+
+// One blind-rotation job of a circuit level: pre-combination sum_k coef_k pool[in[k]] +
+// (0, bconst); coef 0 marks an unused operand.
+struct BrJob {
+    int32_t in[3];
+    int32_t coef[3];
+    uint32_t bconst;
+    int32_t pad;
+};
+
+// One key-switch job: ext rows e1 (+ e2 when e2 >= 0, for MUX) + (0, bconst) -> out row.
+struct KsJob {
+    int32_t e1, e2;
+    uint32_t bconst;
+    int32_t out;
+};
+
+size_t br_smem_bytes();
+cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                      const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms, cudaStream_t st);
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane, uint32_t scale0,
+                              uint32_t scale1, int num_sms, cudaStream_t st);
+cudaError_t launch_precomb_dense(int op, const uint32_t *a, const uint32_t *b, const uint32_t *c, int n,
+                                 size_t count, uint16_t *abar, int abar_stride, int num_sms, cudaStream_t st);
+cudaError_t launch_modswitch(const uint32_t *lwe, int n, size_t jobs, uint16_t *abar, int abar_stride, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32_t *pool, int n, uint16_t *abar,
+                                   int abar_stride, int num_sms, cudaStream_t st);
+cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
+                      const uint32_t *ksk, int n, cudaStream_t st);
+cudaError_t launch_negate(const uint32_t *in, uint32_t *out, size_t words, int num_sms, cudaStream_t st);
+cudaError_t launch_gather(const uint32_t *pool, const int *slots, const uint8_t *neg, size_t cnt, int n,
+                          uint32_t *out, int num_sms, cudaStream_t st);
+cudaError_t launch_trivial(uint32_t *dst, int n, uint32_t b, cudaStream_t st);
+cudaError_t launch_lwe_encrypt(int n, const uint8_t *s, const uint32_t *mask, const uint32_t *noise,
+                               const uint32_t *mu, uint32_t *out, size_t count, int num_sms, cudaStream_t st);
+cudaError_t launch_lwe_phase(int n, const uint8_t *s, const uint32_t *ct, uint32_t *phase, size_t count,
+                             int num_sms, cudaStream_t st);
+cudaError_t launch_keygen_bsk(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                              const uint32_t *noise, uint32_t *bsk, int num_sms, cudaStream_t st);
+cudaError_t launch_keygen_ksk(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                              const uint32_t *noise, uint32_t *ksk, int num_sms, cudaStream_t st);
+
+// Twiddle and constant tables (host side) uploaded at context creation.
+struct NttTables {
+    uint2 ctw[2][2][32];                // warp-uniform stages
+    uint2 lane[2][2][31 * 32];          // lane-dependent stages
+    uint32_t pinv_neg[2];               // Montgomery constants
+    uint2 crt;                          // p0^-1 mod p1 and its Shoup companion
+    uint32_t bsk_scale[2];              // N^-1 2^32 mod p
+};
+void build_ntt_tables(NttTables &t);
+cudaError_t upload_constants(const NttTables &t);
+
+}  // namespace lp

@@ -1,0 +1,577 @@
+// Host side of liblocpir: context, key loading, the C-ABI entry points, NTT tables.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+using namespace lp;
+
+// ---------------------------------------------------------------------------------
+// Errors.
+// ---------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+int lp::fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int lp::cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(LP_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(LP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *lp_strerror(int code)
+{
+    switch (code) {
+    case LP_OK: return "ok";
+    case LP_EINVAL: return "invalid argument";
+    case LP_ENOMEM: return "device out of memory";
+    case LP_ECUDA: return "CUDA error";
+    case LP_ENOKEY: return "keys not loaded";
+    case LP_ETIMEOUT: return "device wait timed out";
+    case LP_EBUSY: return "busy: memory budget exhausted";
+    case LP_ECORRUPT: return "key checksum mismatch";
+    default: return "unknown error";
+    }
+}
+
+extern "C" const char *lp_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------------
+// NTT tables (host arithmetic on 64-bit integers).
+// ---------------------------------------------------------------------------------
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (a * b) % p; }
+static uint64_t powmod(uint64_t b, uint64_t e, uint64_t p)
+{
+    uint64_t r = 1;
+    b %= p;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, p);
+        b = mulmod(b, b, p);
+        e >>= 1;
+    }
+    return r;
+}
+static uint32_t bitrev10(uint32_t x)
+{
+    uint32_t r = 0;
+    for (int i = 0; i < 10; i++) r |= ((x >> i) & 1u) << (9 - i);
+    return r;
+}
+static uint2 shoup_pair(uint64_t w, uint64_t p) { return make_uint2((uint32_t)w, (uint32_t)((w << 32) / p)); }
+
+void lp::build_ntt_tables(NttTables &t)
+{
+    const uint64_t primes[2] = {PRIME0, PRIME1};
+    for (int pi = 0; pi < 2; pi++) {
+        const uint64_t p = primes[pi];
+        // 3 generates the multiplicative group of both primes; psi has order 2N = 2048.
+        const uint64_t psi = powmod(3, (p - 1) / 2048, p);
+        std::vector<uint64_t> zeta(RING_N), izeta(RING_N);
+        for (uint32_t z = 0; z < (uint32_t)RING_N; z++) {
+            zeta[z] = powmod(psi, bitrev10(z), p);
+            izeta[z] = powmod(zeta[z], p - 2, p);
+        }
+        for (int z = 0; z < 32; z++) {
+            t.ctw[pi][0][z] = shoup_pair(zeta[z], p);
+            t.ctw[pi][1][z] = shoup_pair(izeta[z], p);
+        }
+        for (int s = 5; s < 10; s++) {
+            const int L = 512 >> s, base = (1 << (s - 5)) - 1;
+            for (int b = 0; b < 16 / L; b++)
+                for (int lane = 0; lane < 32; lane++) {
+                    const int z = (1 << s) + lane * (16 / L) + b;
+                    t.lane[pi][0][(base + b) * 32 + lane] = shoup_pair(zeta[z], p);
+                    t.lane[pi][1][(base + b) * 32 + lane] = shoup_pair(izeta[z], p);
+                }
+        }
+        // -p^-1 mod 2^32 by Newton iteration (p odd).
+        uint32_t inv = (uint32_t)p;
+        for (int i = 0; i < 5; i++) inv *= 2u - (uint32_t)p * inv;
+        t.pinv_neg[pi] = 0u - inv;
+        // N^-1 2^32 mod p.
+        const uint64_t ninv = powmod(RING_N, p - 2, p);
+        t.bsk_scale[pi] = (uint32_t)mulmod(ninv, (1ull << 32) % p, p);
+    }
+    const uint64_t cinv = powmod(PRIME0 % PRIME1, PRIME1 - 2, PRIME1);
+    t.crt = shoup_pair(cinv, PRIME1);
+}
+
+// ---------------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------------
+int lp::ensure_buf(DevBuf &b, size_t bytes, const char *what)
+{
+    if (b.bytes >= bytes) return LP_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    b.bytes = bytes;
+    return LP_OK;
+}
+
+void lp::free_buf(DevBuf &b)
+{
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+extern "C" int lp_params_default(lp_params *p)
+{
+    if (!p) return fail(LP_EINVAL, "null params");
+    p->n = 630;
+    p->N = 1024;
+    p->k = 1;
+    p->Bgbit = 10;
+    p->lg = 3;
+    p->basebit = 2;
+    p->t = 8;
+    return LP_OK;
+}
+
+static int check_params(const lp_params *p)
+{
+    if (!p) return fail(LP_EINVAL, "null params");
+    if (p->N != RING_N || p->k != 1 || p->Bgbit != BGBIT || p->lg != LG || p->basebit != KS_BASEBIT ||
+        p->t != KS_T)
+        return fail(LP_EINVAL, "unsupported parameters (this build: N=1024 k=1 Bgbit=10 lg=3 basebit=2 t=8)");
+    if (p->n < 1 || p->n > MAX_LWE_N) return fail(LP_EINVAL, "LWE dimension n=%d outside [1, %d]", p->n, MAX_LWE_N);
+    return LP_OK;
+}
+
+extern "C" int lp_create(const lp_params *p, int device, lp_ctx **out)
+{
+    if (!out) return fail(LP_EINVAL, "null output pointer");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(LP_EINVAL, "device %d not present (%d devices)", device, ndev);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if ((size_t)prop.sharedMemPerBlockOptin < br_smem_bytes())
+        return fail(LP_EINVAL, "device offers %zu B shared memory per block, blind rotation needs %zu",
+                    (size_t)prop.sharedMemPerBlockOptin, br_smem_bytes());
+    lp_ctx *c = new lp_ctx();
+    c->params = *p;
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    build_ntt_tables(c->tables);
+    if ((e = upload_constants(c->tables)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "upload constants");
+    }
+    rc = ensure_buf(c->tw_lane, sizeof(c->tables.lane), "twiddle tables");
+    if (!rc) rc = ensure_buf(c->err, sizeof(int), "error word");
+    if (rc) {
+        lp_destroy(c);
+        return rc;
+    }
+    cudaMemcpy(c->tw_lane.ptr, c->tables.lane, sizeof(c->tables.lane), cudaMemcpyHostToDevice);
+    cudaMemset(c->err.ptr, 0, sizeof(int));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        lp_destroy(c);
+        return cuda_fail(e, "context init");
+    }
+    *out = c;
+    return LP_OK;
+}
+
+extern "C" int lp_destroy(lp_ctx *c)
+{
+    if (!c) return LP_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &t : c->timers) {
+        for (auto &ev : t.second.pending) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+    }
+    for (DevBuf *b : {&c->tw_lane, &c->err, &c->bsk_hat, &c->ksk, &c->abar, &c->ext, &c->pool, &c->jobs,
+                      &c->tmp_in, &c->tmp_out})
+        free_buf(*b);
+    delete c;
+    return LP_OK;
+}
+
+int lp::ctx_check_err(lp_ctx *c)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read device error word");
+    if (h) {
+        cudaMemset(c->err.ptr, 0, sizeof(int));
+        if (h & DEV_ERR_TIMEOUT) return fail(LP_ETIMEOUT, "a device-side wait timed out");
+        return fail(LP_ECUDA, "device error word 0x%x", h);
+    }
+    return LP_OK;
+}
+
+extern "C" int lp_sync(lp_ctx *c)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return ctx_check_err(c);
+}
+
+// ---------------------------------------------------------------------------------
+// Timing of library kernels with CUDA events on the launching stream.
+// ---------------------------------------------------------------------------------
+void lp::timer_begin(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t *ev0)
+{
+    *ev0 = nullptr;
+    if (!c->timing) return;
+    cudaEventCreate(ev0);
+    cudaEventRecord(*ev0, st);
+    (void)name;
+}
+
+void lp::timer_end(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t ev0)
+{
+    if (!c->timing || !ev0) return;
+    cudaEvent_t ev1;
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev1, st);
+    c->timers[name].pending.emplace_back(ev0, ev1);
+}
+
+extern "C" int lp_set_timing(lp_ctx *c, int enable)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    c->timing = enable != 0;
+    return LP_OK;
+}
+
+extern "C" int lp_kernel_time(lp_ctx *c, const char *kernel, double *ms_total, uint64_t *launches)
+{
+    if (!c || !kernel || !ms_total || !launches) return fail(LP_EINVAL, "null argument");
+    cudaSetDevice(c->device);
+    auto it = c->timers.find(kernel);
+    *ms_total = 0.0;
+    *launches = 0;
+    if (it == c->timers.end()) return LP_OK;
+    KernelTimer &t = it->second;
+    for (auto &ev : t.pending) {
+        cudaError_t e = cudaEventSynchronize(ev.second);
+        if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev.first, ev.second);
+        t.ms += ms;
+        t.count += 1;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    t.pending.clear();
+    *ms_total = t.ms;
+    *launches = t.count;
+    return LP_OK;
+}
+
+extern "C" int lp_reset_timing(lp_ctx *c)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    double ms;
+    uint64_t n;
+    for (auto &kv : c->timers) lp_kernel_time(c, kv.first.c_str(), &ms, &n);
+    c->timers.clear();
+    return LP_OK;
+}
+
+extern "C" uint64_t lp_launch_count(const lp_ctx *c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------------------------------
+// Keys.
+// ---------------------------------------------------------------------------------
+static size_t bsk_words(const lp_params &p) { return (size_t)p.n * ROWS * 2 * RING_N; }
+static size_t ksk_words(const lp_params &p) { return (size_t)RING_N * KS_T * KS_BASE * (p.n + 1); }
+
+static int load_bsk_common(lp_ctx *c, const uint32_t *src, bool on_device, size_t words, cudaStream_t st)
+{
+    if (!c || !src) return fail(LP_EINVAL, "null argument");
+    if (words != bsk_words(c->params))
+        return fail(LP_EINVAL, "bootstrapping key has %zu words, expected %zu", words, bsk_words(c->params));
+    cudaSetDevice(c->device);
+    int rc = ensure_buf(c->bsk_hat, words * 2 * sizeof(uint32_t), "bootstrapping key");
+    if (rc) return rc;
+    DevBuf coef;
+    const uint32_t *dsrc = src;
+    if (!on_device) {
+        rc = ensure_buf(coef, words * sizeof(uint32_t), "bootstrapping key staging");
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(coef.ptr, src, words * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            free_buf(coef);
+            return cuda_fail(e, "copy bootstrapping key");
+        }
+        dsrc = static_cast<const uint32_t *>(coef.ptr);
+    }
+    cudaError_t e = launch_bsk_to_ntt(dsrc, static_cast<uint32_t *>(c->bsk_hat.ptr), c->params.n,
+                                      static_cast<const uint2 *>(c->tw_lane.ptr), c->tables.bsk_scale[0],
+                                      c->tables.bsk_scale[1], c->num_sms, st);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_buf(coef);
+    if (e != cudaSuccess) return cuda_fail(e, "convert bootstrapping key");
+    c->have_bsk = true;
+    return LP_OK;
+}
+
+extern "C" int lp_load_bsk(lp_ctx *c, const uint32_t *bsk, size_t words)
+{
+    return load_bsk_common(c, bsk, false, words, 0);
+}
+
+extern "C" int lp_load_bsk_device(lp_ctx *c, const uint32_t *bsk, size_t words, void *stream)
+{
+    return load_bsk_common(c, bsk, true, words, static_cast<cudaStream_t>(stream));
+}
+
+static int load_ksk_common(lp_ctx *c, const uint32_t *src, bool on_device, size_t words, cudaStream_t st)
+{
+    if (!c || !src) return fail(LP_EINVAL, "null argument");
+    if (words != ksk_words(c->params))
+        return fail(LP_EINVAL, "key-switching key has %zu words, expected %zu", words, ksk_words(c->params));
+    cudaSetDevice(c->device);
+    int rc = ensure_buf(c->ksk, words * sizeof(uint32_t), "key-switching key");
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->ksk.ptr, src, words * 4,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy key-switching key");
+    c->have_ksk = true;
+    return LP_OK;
+}
+
+extern "C" int lp_load_ksk(lp_ctx *c, const uint32_t *ksk, size_t words)
+{
+    return load_ksk_common(c, ksk, false, words, 0);
+}
+
+extern "C" int lp_load_ksk_device(lp_ctx *c, const uint32_t *ksk, size_t words, void *stream)
+{
+    return load_ksk_common(c, ksk, true, words, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------------
+// Bootstrap pipeline pieces shared by the batch and circuit entry points.
+// ---------------------------------------------------------------------------------
+int lp::abar_stride(const lp_ctx *c) { return ((c->params.n + 1) + 7) & ~7; }
+
+int lp::ensure_scratch(lp_ctx *c, size_t br_jobs)
+{
+    int rc = ensure_buf(c->abar, br_jobs * abar_stride(c) * sizeof(uint16_t), "mod-switched scratch");
+    if (!rc) rc = ensure_buf(c->ext, br_jobs * EXT_STRIDE * sizeof(uint32_t), "extracted-sample scratch");
+    return rc;
+}
+
+int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
+{
+    cudaEvent_t ev0;
+    timer_begin(c, "br", st, &ev0);
+    cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
+                              static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                              static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
+                              static_cast<int *>(c->err.ptr), c->num_sms, st);
+    timer_end(c, "br", st, ev0);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
+    return LP_OK;
+}
+
+int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st)
+{
+    cudaEvent_t ev0;
+    timer_begin(c, "ks", st, &ev0);
+    cudaError_t e = launch_ks(static_cast<const uint32_t *>(c->ext.ptr), jobs, njobs, dense_mux, out,
+                              static_cast<const uint32_t *>(c->ksk.ptr), c->params.n, st);
+    timer_end(c, "ks", st, ev0);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
+    return LP_OK;
+}
+
+// Largest number of blind-rotation jobs one pass handles (bounds the scratch to ~0.6 GB).
+static const size_t MAX_PASS_JOBS = 131072;
+
+extern "C" int lp_gate_batch(lp_ctx *c, int op, const uint32_t *a, const uint32_t *b, const uint32_t *cc,
+                             uint32_t *out, size_t count, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (op < LP_NAND || op > LP_MUX) return fail(LP_EINVAL, "unknown gate %d", op);
+    if (count == 0) return LP_OK;
+    if (!a || !out || (op != LP_NOT && !b) || (op == LP_MUX && !cc)) return fail(LP_EINVAL, "null ciphertext pointer");
+    cudaSetDevice(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = c->params.n;
+    const size_t W = (size_t)n + 1;
+    if (op == LP_NOT) {
+        cudaError_t e = launch_negate(a, out, count * W, c->num_sms, st);
+        c->launches++;
+        return e == cudaSuccess ? LP_OK : cuda_fail(e, "negate launch");
+    }
+    if (!c->have_bsk || !c->have_ksk) return fail(LP_ENOKEY, "load the bootstrapping and key-switching keys first");
+    const size_t halves = op == LP_MUX ? 2 : 1;
+    const size_t per_pass = MAX_PASS_JOBS / halves;
+    int rc = ensure_scratch(c, (count < per_pass ? count : per_pass) * halves);
+    if (rc) return rc;
+    for (size_t off = 0; off < count; off += per_pass) {
+        const size_t cnt = count - off < per_pass ? count - off : per_pass;
+        cudaError_t e = launch_precomb_dense(op, a + off * W, b + off * W, op == LP_MUX ? cc + off * W : nullptr, n,
+                                             cnt, static_cast<uint16_t *>(c->abar.ptr), abar_stride(c),
+                                             c->num_sms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
+        if ((rc = run_br(c, cnt * halves, T_EIGHTH, st))) return rc;
+        if ((rc = run_ks(c, nullptr, cnt, op == LP_MUX, out + off * W, st))) return rc;
+    }
+    return LP_OK;
+}
+
+extern "C" int lp_gate_batch_host(lp_ctx *c, int op, const uint32_t *a, const uint32_t *b, const uint32_t *cc,
+                                  uint32_t *out, size_t count)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (count == 0) return LP_OK;
+    if (op < LP_NAND || op > LP_MUX) return fail(LP_EINVAL, "unknown gate %d", op);
+    if (!a || !out || (op != LP_NOT && !b) || (op == LP_MUX && !cc)) return fail(LP_EINVAL, "null ciphertext pointer");
+    cudaSetDevice(c->device);
+    const size_t W = (size_t)c->params.n + 1, bytes = count * W * 4;
+    const int nin = op == LP_NOT ? 1 : (op == LP_MUX ? 3 : 2);
+    int rc = ensure_buf(c->tmp_in, bytes * nin, "host-batch input staging");
+    if (!rc) rc = ensure_buf(c->tmp_out, bytes, "host-batch output staging");
+    if (rc) return rc;
+    uint32_t *din = static_cast<uint32_t *>(c->tmp_in.ptr);
+    const uint32_t *srcs[3] = {a, b, cc};
+    for (int k = 0; k < nin; k++) {
+        cudaError_t e = cudaMemcpyAsync(din + k * count * W, srcs[k], bytes, cudaMemcpyHostToDevice, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "copy inputs");
+    }
+    rc = lp_gate_batch(c, op, din, nin > 1 ? din + count * W : nullptr, nin > 2 ? din + 2 * count * W : nullptr,
+                       static_cast<uint32_t *>(c->tmp_out.ptr), count, 0);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(out, c->tmp_out.ptr, bytes, cudaMemcpyDeviceToHost, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+    return ctx_check_err(c);
+}
+
+extern "C" int lp_bootstrap_extract(lp_ctx *c, const uint32_t *lwe, uint32_t mu, uint32_t *ext, size_t count,
+                                    void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (count == 0) return LP_OK;
+    if (!lwe || !ext) return fail(LP_EINVAL, "null pointer");
+    if (!c->have_bsk) return fail(LP_ENOKEY, "load the bootstrapping key first");
+    cudaSetDevice(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = c->params.n;
+    int rc = ensure_scratch(c, count < MAX_PASS_JOBS ? count : MAX_PASS_JOBS);
+    if (rc) return rc;
+    for (size_t off = 0; off < count; off += MAX_PASS_JOBS) {
+        const size_t cnt = count - off < MAX_PASS_JOBS ? count - off : MAX_PASS_JOBS;
+        cudaError_t e = launch_modswitch(lwe + off * (n + 1), n, cnt, static_cast<uint16_t *>(c->abar.ptr),
+                                         abar_stride(c), c->num_sms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "modulus switch launch");
+        if ((rc = run_br(c, cnt, mu, st))) return rc;
+        e = cudaMemcpy2DAsync(ext + off * (RING_N + 1), (RING_N + 1) * 4, c->ext.ptr, EXT_STRIDE * 4,
+                              (RING_N + 1) * 4, cnt, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy extracted samples");
+    }
+    return LP_OK;
+}
+
+extern "C" int lp_key_switch(lp_ctx *c, const uint32_t *ext, uint32_t *out, size_t count, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (count == 0) return LP_OK;
+    if (!ext || !out) return fail(LP_EINVAL, "null pointer");
+    if (!c->have_ksk) return fail(LP_ENOKEY, "load the key-switching key first");
+    cudaSetDevice(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = c->params.n;
+    int rc = ensure_scratch(c, count < MAX_PASS_JOBS ? count : MAX_PASS_JOBS);
+    if (rc) return rc;
+    for (size_t off = 0; off < count; off += MAX_PASS_JOBS) {
+        const size_t cnt = count - off < MAX_PASS_JOBS ? count - off : MAX_PASS_JOBS;
+        cudaError_t e = cudaMemcpy2DAsync(c->ext.ptr, EXT_STRIDE * 4, ext + off * (RING_N + 1), (RING_N + 1) * 4,
+                                          (RING_N + 1) * 4, cnt, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage extracted samples");
+        if ((rc = run_ks(c, nullptr, cnt, 0, out + off * (n + 1), st))) return rc;
+    }
+    return LP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Client side.
+// ---------------------------------------------------------------------------------
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+extern "C" int lp_client_lwe_encrypt(int n, const uint8_t *s, const uint32_t *mask, const uint32_t *noise,
+                                     const uint32_t *mu, uint32_t *out, size_t count, void *stream)
+{
+    if (n < 1 || n > MAX_LWE_N) return fail(LP_EINVAL, "bad n=%d", n);
+    if (count == 0) return LP_OK;
+    if (!s || !mask || !noise || !mu || !out) return fail(LP_EINVAL, "null pointer");
+    cudaError_t e = launch_lwe_encrypt(n, s, mask, noise, mu, out, count, device_sms(), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "encrypt launch");
+}
+
+extern "C" int lp_client_lwe_phase(int n, const uint8_t *s, const uint32_t *ct, uint32_t *phase, size_t count,
+                                   void *stream)
+{
+    if (n < 1 || n > MAX_LWE_N) return fail(LP_EINVAL, "bad n=%d", n);
+    if (count == 0) return LP_OK;
+    if (!s || !ct || !phase) return fail(LP_EINVAL, "null pointer");
+    cudaError_t e = launch_lwe_phase(n, s, ct, phase, count, device_sms(), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "phase launch");
+}
+
+extern "C" int lp_client_keygen_bsk(const lp_params *p, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                                    const uint32_t *noise, uint32_t *bsk, void *stream)
+{
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!s || !S || !mask || !noise || !bsk) return fail(LP_EINVAL, "null pointer");
+    cudaError_t e = launch_keygen_bsk(p->n, s, S, mask, noise, bsk, device_sms(), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "keygen_bsk launch");
+}
+
+extern "C" int lp_client_keygen_ksk(const lp_params *p, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
+                                    const uint32_t *noise, uint32_t *ksk, void *stream)
+{
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!s || !S || !mask || !noise || !ksk) return fail(LP_EINVAL, "null pointer");
+    cudaError_t e = launch_keygen_ksk(p->n, s, S, mask, noise, ksk, device_sms(), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "keygen_ksk launch");
+}

@@ -1,0 +1,56 @@
+// Context structure and host helpers of liblocpir (internal).
+#pragma once
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/locpir.h"
+#include "kernels.h"
+
+namespace lp {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct KernelTimer {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0.0;
+    uint64_t count = 0;
+};
+
+}  // namespace lp
+
+struct lp_ctx {
+    lp_params params{};
+    int device = 0;
+    int num_sms = 1;
+    lp::NttTables tables{};
+    lp::DevBuf tw_lane, err;        // lane twiddles, device error word
+    lp::DevBuf bsk_hat, ksk;        // keys (transform-domain BSK, coefficient KSK)
+    lp::DevBuf abar, ext;           // per-pass scratch: mod-switched inputs, extracted samples
+    lp::DevBuf pool, jobs;          // circuit ciphertext pool and job records
+    lp::DevBuf tmp_in, tmp_out;     // staging of the host-pointer entry points
+    bool have_bsk = false, have_ksk = false;
+    bool timing = false;
+    uint64_t launches = 0;
+    std::map<std::string, lp::KernelTimer> timers;
+};
+
+namespace lp {
+
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+int ensure_buf(DevBuf &b, size_t bytes, const char *what);
+void free_buf(DevBuf &b);
+int ctx_check_err(lp_ctx *c);
+int abar_stride(const lp_ctx *c);
+int ensure_scratch(lp_ctx *c, size_t br_jobs);
+int run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);
+int run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);
+void timer_begin(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t *ev0);
+void timer_end(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t ev0);
+
+}  // namespace lp

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of liblocpir.so (include/locpir.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes pointers and
+sizes straight through; all arithmetic runs in the library's CUDA kernels.  Device
+ciphertext arguments are torch tensors on the context's CUDA device (int32 or uint32,
+contiguous, [count][n + 1]); host arguments of the *_host / key-loading calls are numpy
+uint32 arrays.  A missing library raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblocpir.so")
+
+LP_OK, LP_EINVAL, LP_ENOMEM, LP_ECUDA, LP_ENOKEY, LP_ETIMEOUT, LP_EBUSY, LP_ECORRUPT = 0, -1, -2, -3, -4, -5, -6, -7
+LP_NAND, LP_AND, LP_OR, LP_XOR, LP_XNOR, LP_NOT, LP_MUX = range(7)
+LP_LT, LP_LE = 0, 1
+LP_XOR_TREE, LP_XOR_CHAIN, LP_OR_TREE = 0, 1, 2
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTS = [
+    "lp_params_default", "lp_create", "lp_destroy", "lp_sync", "lp_strerror", "lp_last_error",
+    "lp_load_bsk", "lp_load_bsk_device", "lp_load_ksk", "lp_load_ksk_device",
+    "lp_gate_batch", "lp_gate_batch_host", "lp_bootstrap_extract", "lp_key_switch",
+    "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch",
+    "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
+    "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
+]
+
+
+class lp_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("n", "N", "k", "Bgbit", "lg", "basebit", "t")]
+
+
+class lp_query(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("is_signed", ctypes.c_int), ("n_boxes", ctypes.c_int), ("m", ctypes.c_int),
+                ("comb", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("boxes", ctypes.c_void_p),
+                ("services", ctypes.c_void_p), ("out_service", ctypes.c_void_p)]
+
+
+class LocpirError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblocpir.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2407_19871_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32
+        P = ctypes.POINTER(lp_params)
+        sig = {
+            "lp_params_default": (i, [P]),
+            "lp_create": (i, [P, i, ctypes.POINTER(vp)]),
+            "lp_destroy": (i, [vp]),
+            "lp_sync": (i, [vp]),
+            "lp_strerror": (ctypes.c_char_p, [i]),
+            "lp_last_error": (ctypes.c_char_p, []),
+            "lp_load_bsk": (i, [vp, vp, sz]),
+            "lp_load_bsk_device": (i, [vp, vp, sz, vp]),
+            "lp_load_ksk": (i, [vp, vp, sz]),
+            "lp_load_ksk_device": (i, [vp, vp, sz, vp]),
+            "lp_gate_batch": (i, [vp, i, vp, vp, vp, vp, sz, vp]),
+            "lp_gate_batch_host": (i, [vp, i, vp, vp, vp, vp, sz]),
+            "lp_bootstrap_extract": (i, [vp, vp, u32, vp, sz, vp]),
+            "lp_key_switch": (i, [vp, vp, vp, sz, vp]),
+            "lp_compare_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
+            "lp_locpir_query": (i, [vp, i, i, vp, vp, i, vp, i, vp, i, vp, vp]),
+            "lp_locpir_batch": (i, [vp, ctypes.POINTER(lp_query), sz, vp]),
+            "lp_client_lwe_encrypt": (i, [i, vp, vp, vp, vp, vp, sz, vp]),
+            "lp_client_lwe_phase": (i, [i, vp, vp, vp, sz, vp]),
+            "lp_client_keygen_bsk": (i, [P, vp, vp, vp, vp, vp, vp]),
+            "lp_client_keygen_ksk": (i, [P, vp, vp, vp, vp, vp, vp]),
+            "lp_launch_count": (ctypes.c_uint64, [vp]),
+            "lp_set_timing": (i, [vp, i]),
+            "lp_kernel_time": (i, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+            "lp_reset_timing": (i, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != LP_OK:
+        raise LocpirError(code, where, lib().lp_last_error().decode())
+
+
+def _dptr(t, words: int | None = None, name: str = "tensor") -> int | None:
+    """Device pointer of a contiguous CUDA tensor of 32-bit (or 8-bit key) elements."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if words is not None and t.numel() < words:
+        raise ValueError(f"{name} has {t.numel()} elements, the call reads {words}")
+    return t.data_ptr()
+
+
+def _hptr(a: np.ndarray) -> int:
+    if not (a.flags["C_CONTIGUOUS"] and a.dtype == np.uint32):
+        raise ValueError("host arrays must be C-contiguous uint32")
+    return a.ctypes.data
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def params_default() -> lp_params:
+    p = lp_params()
+    _check(lib().lp_params_default(ctypes.byref(p)), "lp_params_default")
+    return p
+
+
+def lp_client_lwe_encrypt(n, s, mask, noise, mu, out, count, stream=None):
+    _check(lib().lp_client_lwe_encrypt(n, _dptr(s), _dptr(mask), _dptr(noise), _dptr(mu), _dptr(out), count,
+                                       _stream(stream)), "lp_client_lwe_encrypt")
+
+
+def lp_client_lwe_phase(n, s, ct, phase, count, stream=None):
+    _check(lib().lp_client_lwe_phase(n, _dptr(s), _dptr(ct), _dptr(phase), count, _stream(stream)),
+           "lp_client_lwe_phase")
+
+
+def lp_client_keygen_bsk(params, s, S, mask, noise, bsk, stream=None):
+    _check(lib().lp_client_keygen_bsk(ctypes.byref(params), _dptr(s), _dptr(S), _dptr(mask), _dptr(noise),
+                                      _dptr(bsk), _stream(stream)), "lp_client_keygen_bsk")
+
+
+def lp_client_keygen_ksk(params, s, S, mask, noise, ksk, stream=None):
+    _check(lib().lp_client_keygen_ksk(ctypes.byref(params), _dptr(s), _dptr(S), _dptr(mask), _dptr(noise),
+                                      _dptr(ksk), _stream(stream)), "lp_client_keygen_ksk")
+
+
+class Context:
+    """An lp_ctx: keys and scratch on one device.  Methods mirror the lp_* entry points."""
+
+    def __init__(self, device: int = 0, params: lp_params | None = None):
+        self.params = params or params_default()
+        h = ctypes.c_void_p()
+        _check(lib().lp_create(ctypes.byref(self.params), device, ctypes.byref(h)), "lp_create")
+        self.h = h
+        self.device = device
+        self.n = self.params.n
+        self.N = self.params.N
+
+    def close(self) -> None:
+        if self.h:
+            lib().lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- keys
+    def lp_load_bsk(self, bsk: np.ndarray) -> None:
+        _check(lib().lp_load_bsk(self.h, _hptr(bsk), bsk.size), "lp_load_bsk")
+
+    def lp_load_ksk(self, ksk: np.ndarray) -> None:
+        _check(lib().lp_load_ksk(self.h, _hptr(ksk), ksk.size), "lp_load_ksk")
+
+    def lp_load_bsk_device(self, bsk, stream=None) -> None:
+        _check(lib().lp_load_bsk_device(self.h, _dptr(bsk), bsk.numel(), _stream(stream)), "lp_load_bsk_device")
+
+    def lp_load_ksk_device(self, ksk, stream=None) -> None:
+        _check(lib().lp_load_ksk_device(self.h, _dptr(ksk), ksk.numel(), _stream(stream)), "lp_load_ksk_device")
+
+    # ---- bootstrapping
+    def lp_gate_batch(self, op: int, a, b, c, out, count: int, stream=None) -> None:
+        W = count * (self.n + 1)
+        _check(lib().lp_gate_batch(self.h, op, _dptr(a, W, "a"), _dptr(b, W, "b") if b is not None else None,
+                                   _dptr(c, W, "c") if c is not None else None, _dptr(out, W, "out"), count,
+                                   _stream(stream)), "lp_gate_batch")
+
+    def lp_gate_batch_host(self, op: int, a: np.ndarray, b, c, out: np.ndarray, count: int) -> None:
+        _check(lib().lp_gate_batch_host(self.h, op, _hptr(a), _hptr(b) if b is not None else None,
+                                        _hptr(c) if c is not None else None, _hptr(out), count),
+               "lp_gate_batch_host")
+
+    def lp_bootstrap_extract(self, lwe, mu: int, ext, count: int, stream=None) -> None:
+        _check(lib().lp_bootstrap_extract(self.h, _dptr(lwe, count * (self.n + 1), "lwe"), mu & 0xFFFFFFFF,
+                                          _dptr(ext, count * (self.N + 1), "ext"), count, _stream(stream)),
+               "lp_bootstrap_extract")
+
+    def lp_key_switch(self, ext, out, count: int, stream=None) -> None:
+        _check(lib().lp_key_switch(self.h, _dptr(ext, count * (self.N + 1), "ext"),
+                                   _dptr(out, count * (self.n + 1), "out"), count, _stream(stream)), "lp_key_switch")
+
+    # ---- circuits
+    def lp_compare_batch(self, kind: int, is_signed: int, l: int, x1, x2, out, count: int, stream=None) -> None:
+        W = self.n + 1
+        _check(lib().lp_compare_batch(self.h, kind, is_signed, l, _dptr(x1, count * l * W, "x1"),
+                                      _dptr(x2, count * l * W, "x2"), _dptr(out, count * W, "out"), count,
+                                      _stream(stream)), "lp_compare_batch")
+
+    def lp_locpir_query(self, l, is_signed, x, y, n_boxes, boxes, m, services, comb, out_service, stream=None):
+        W = self.n + 1
+        _check(lib().lp_locpir_query(self.h, l, is_signed, _dptr(x, l * W, "x"), _dptr(y, l * W, "y"), n_boxes,
+                                     _dptr(boxes, n_boxes * 4 * l * W, "boxes"), m,
+                                     _dptr(services, n_boxes * m * W, "services"), comb,
+                                     _dptr(out_service, m * W, "out_service"), _stream(stream)), "lp_locpir_query")
+
+    def lp_locpir_batch(self, queries: list[dict], stream=None) -> None:
+        """queries: dicts with l, is_signed, n_boxes, m, comb and tensors x, y, boxes,
+        services, out_service (shapes as in lp_locpir_query)."""
+        W = self.n + 1
+        arr = (lp_query * len(queries))()
+        for i, q in enumerate(queries):
+            l, nb, m = q["l"], q["n_boxes"], q["m"]
+            arr[i] = lp_query(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
+                              _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"),
+                              _dptr(q["boxes"], nb * 4 * l * W, "boxes"), _dptr(q["services"], nb * m * W, "services"),
+                              _dptr(q["out_service"], m * W, "out_service"))
+        _check(lib().lp_locpir_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_batch")
+
+    # ---- runtime
+    def lp_sync(self) -> None:
+        _check(lib().lp_sync(self.h), "lp_sync")
+
+    def lp_launch_count(self) -> int:
+        return int(lib().lp_launch_count(self.h))
+
+    def lp_set_timing(self, enable: bool) -> None:
+        _check(lib().lp_set_timing(self.h, int(bool(enable))), "lp_set_timing")
+
+    def lp_kernel_time(self, kernel: str) -> tuple[float, int]:
+        ms, cnt = ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().lp_kernel_time(self.h, kernel.encode(), ctypes.byref(ms), ctypes.byref(cnt)), "lp_kernel_time")
+        return ms.value, cnt.value
+
+    def lp_reset_timing(self) -> None:
+        _check(lib().lp_reset_timing(self.h), "lp_reset_timing")

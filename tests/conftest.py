@@ -4,8 +4,9 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-if ROOT not in sys.path:
-    sys.path.insert(0, ROOT)
+for _p in (ROOT, os.path.dirname(os.path.abspath(__file__))):
+    if _p not in sys.path:
+        sys.path.insert(0, _p)
 
 
 def pytest_configure(config):
@@ -41,3 +42,20 @@ def keys_trivial():
     import oracle
     import synth
     return oracle.keygen(synth.key_draws(11, noiseless=True, zero_masks=True))
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx(keys):
+    """Library context on cuda:0 with the seed-0 keys (generated by the oracle) loaded."""
+    from gpu_util import make_context
+    ctx = make_context(keys)
+    yield ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx_trivial(keys_trivial):
+    from gpu_util import make_context
+    ctx = make_context(keys_trivial)
+    yield ctx
+    ctx.close()
