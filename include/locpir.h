@@ -118,6 +118,24 @@ int lp_gate_batch(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, con
 int lp_gate_batch_host(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
                        uint32_t *out, size_t count);
 
+/* lp_gate_batch_noalloc: the same gates as lp_gate_batch, computed by the same kernels, for
+ * callers that must not allocate device memory while they evaluate -- e.g. a server whose
+ * device memory is handed out up front by its own allocator and budget, or a latency-critical
+ * loop that cannot absorb the device-wide synchronisation of cudaMalloc / cudaFree.  (The
+ * paper has no counterpart; this is a deployment variant of the gate batch.)
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its scratch (the
+ * mod-switched inputs and the extracted samples) is a fixed array of about 1.5 MiB compiled
+ * into the library, held by every GPU that loads the library until the process exits.
+ * Limit: at most 256 blind rotations per call (count <= 256 for two-input gates, <= 128 for
+ * MUX; NOT uses no scratch); larger counts return LP_EINVAL.  The first call on a device looks
+ * up the array's device address with that device current (a one-time set-up per device); make
+ * that first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (nothing in it needs clearing: every word read is written earlier in the same
+ * call), so calls that overlap on the GPU race: issue them in order on one stream.  Keys must be
+ * loaded (LP_ENOKEY otherwise); pointers and layout as in lp_gate_batch. */
+int lp_gate_batch_noalloc(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                          uint32_t *out, size_t count, void *stream);
+
 /* The two halves of a bootstrap, exposed for step-level parity checks.
  * lp_bootstrap_extract: count LWEs [count][n + 1] -> modulus switch, blind rotation with
  * test vector v_j = mu for all j, sample extraction -> [count][N + 1] N-LWEs under S.

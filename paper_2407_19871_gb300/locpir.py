@@ -25,7 +25,7 @@ LP_XOR_TREE, LP_XOR_CHAIN, LP_OR_TREE = 0, 1, 2
 EXPORTS = [
     "lp_params_default", "lp_create", "lp_destroy", "lp_sync", "lp_strerror", "lp_last_error",
     "lp_load_bsk", "lp_load_bsk_device", "lp_load_ksk", "lp_load_ksk_device",
-    "lp_gate_batch", "lp_gate_batch_host", "lp_bootstrap_extract", "lp_key_switch",
+    "lp_gate_batch", "lp_gate_batch_host", "lp_gate_batch_noalloc", "lp_bootstrap_extract", "lp_key_switch",
     "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch",
     "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
     "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "lp_load_ksk_device": (i, [vp, vp, sz, vp]),
             "lp_gate_batch": (i, [vp, i, vp, vp, vp, vp, sz, vp]),
             "lp_gate_batch_host": (i, [vp, i, vp, vp, vp, vp, sz]),
+            "lp_gate_batch_noalloc": (i, [vp, i, vp, vp, vp, vp, sz, vp]),
             "lp_bootstrap_extract": (i, [vp, vp, u32, vp, sz, vp]),
             "lp_key_switch": (i, [vp, vp, vp, sz, vp]),
             "lp_compare_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
@@ -206,6 +207,14 @@ class Context:
         _check(lib().lp_gate_batch_host(self.h, op, _hptr(a), _hptr(b) if b is not None else None,
                                         _hptr(c) if c is not None else None, _hptr(out), count),
                "lp_gate_batch_host")
+
+    def lp_gate_batch_noalloc(self, op: int, a, b, c, out, count: int, stream=None) -> None:
+        """lp_gate_batch without device allocation: scratch in the library's fixed array
+        (at most 256 blind rotations per call)."""
+        W = count * (self.n + 1)
+        _check(lib().lp_gate_batch_noalloc(self.h, op, _dptr(a, W, "a"), _dptr(b, W, "b") if b is not None else None,
+                                           _dptr(c, W, "c") if c is not None else None, _dptr(out, W, "out"), count,
+                                           _stream(stream)), "lp_gate_batch_noalloc")
 
     def lp_bootstrap_extract(self, lwe, mu: int, ext, count: int, stream=None) -> None:
         _check(lib().lp_bootstrap_extract(self.h, _dptr(lwe, count * (self.n + 1), "lwe"), mu & 0xFFFFFFFF,
