@@ -11,7 +11,8 @@
 // hold up to 255 registers):
 //   Warp w serves ciphertext slot w / 2 and NTT prime w % 2; the two warps of a slot (a
 //   "pair") split the external product by prime and meet twice per step (named barrier
-//   1 + slot, 64 threads).
+//   1 + slot, 64 threads).  Both primes run the same code (the prime is a runtime value),
+//   which keeps the kernel inside the instruction caches.
 //   Key chunks (one chunk = row r of BSK_i for one prime, both TRLWE components, 8 KB)
 //   flow through a ring of BR_RING shared-memory slots per prime.  Lane 0 of the slot-0
 //   warp of each prime is also that prime's producer: it issues cp.async.bulk copies
@@ -20,10 +21,12 @@
 //   chunks ahead.  All waits are bounded (LP_ETIMEOUT on expiry).
 //
 // Per step and pair: both warps rotate/subtract ACC (shared memory) and decompose it;
-// each warp forward-transforms the 6 digit polynomials modulo its prime, multiplies them
-// with the key chunk (Montgomery, key stored as NTT(b) N^-1 2^32 mod p) accumulating both
-// output components, inverse-transforms the 2 sums; the prime-0 warp hands its residues
-// over shared memory; the prime-1 warp recombines them (centred CRT) and adds to ACC.
+// each warp forward-transforms the 6 digit polynomials modulo its prime and multiplies
+// them with the key chunk, accumulating both output components in 64-bit registers
+// (key stored as NTT(b) N^-1 2^32 mod p, one Montgomery reduction per coefficient);
+// it inverse-transforms the 2 sums.  The pair then swaps half of its residues through
+// shared memory: the prime-0 warp recombines component 0 (centred CRT) and adds it to
+// ACC, the prime-1 warp component 1.
 #include "common.cuh"
 #include "kernels.h"
 #include "ntt.cuh"
@@ -71,63 +74,61 @@ struct Producer {
     uint32_t total;
     uint32_t issued;
     int n;
+    int pi;
 };
 
-template <int PI>
 __device__ __forceinline__ void produce(BrSmem &sm, Producer &pr, uint32_t upto)
 {
-    // Issue chunks [pr.issued, min(upto, total)) into their ring slots; slot of chunk q
+    // Issue chunks [pr.issued, min(upto, total)) into their ring slots; the slot of chunk q
     // is free once chunk q - BR_RING was released by all consumers.
     while (pr.issued < upto && pr.issued < pr.total) {
         const uint32_t q = pr.issued;
         const uint32_t s = q % BR_RING;
         if (q >= (uint32_t)BR_RING) {
             const uint32_t par = ((q - BR_RING) / BR_RING) & 1u;
-            if (!mbar_wait_bounded(&sm.empty_bar[PI][s], par, &sm.abort)) {
+            if (!mbar_wait_bounded(&sm.empty_bar[pr.pi][s], par, &sm.abort)) {
                 *reinterpret_cast<volatile int *>(&sm.abort) = 1;
                 return;
             }
         }
         const int r = (int)(q % ROWS);
         const int i = (int)((q / ROWS) % (uint32_t)pr.n);
-        mbar_arrive_expect_tx(&sm.full_bar[PI][s], CHUNK_BYTES);
-        const uint32_t *src = pr.bsk_hat + ((size_t)(i * 2 + PI) * ROWS + r) * CHUNK_WORDS;
-        bulk_copy_g2s(sm.ring[PI][s], src, CHUNK_BYTES, &sm.full_bar[PI][s]);
+        mbar_arrive_expect_tx(&sm.full_bar[pr.pi][s], CHUNK_BYTES);
+        const uint32_t *src = pr.bsk_hat + ((size_t)(i * 2 + pr.pi) * ROWS + r) * CHUNK_WORDS;
+        bulk_copy_g2s(sm.ring[pr.pi][s], src, CHUNK_BYTES, &sm.full_bar[pr.pi][s]);
         pr.issued++;
     }
 }
 
 // Wait (bounded) until every chunk issued by this producer has landed in shared memory.
-template <int PI>
 __device__ __forceinline__ bool drain(BrSmem &sm, const Producer &pr)
 {
     bool ok = true;
     const uint32_t first = pr.issued > (uint32_t)BR_RING ? pr.issued - BR_RING : 0u;
     volatile int never = 0;
     for (uint32_t q = first; q < pr.issued; q++)
-        ok &= mbar_wait_bounded(&sm.full_bar[PI][q % BR_RING], (q / BR_RING) & 1u, &never);
+        ok &= mbar_wait_bounded(&sm.full_bar[pr.pi][q % BR_RING], (q / BR_RING) & 1u, &never);
     return ok;
 }
 
-// One external-product half for prime PI: rotate/decompose ACC, 6 forward NTTs each
-// followed by the multiply-accumulate with the streamed key chunk, 2 inverse NTTs.
-// On return acc0 / acc1 hold the two output components mod p in [0, p), layout A.
-template <int PI>
-__device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane, int ab, bool work,
-                                                 uint32_t &cseq, uint32_t (&acc0)[32], uint32_t (&acc1)[32],
-                                                 uint32_t *tbuf, Producer &pr, bool producer)
+// One external-product half for prime pi: rotate/decompose ACC, 6 forward NTTs each
+// followed by the 64-bit multiply-accumulate with the streamed key chunk, 2 inverse NTTs.
+// On return `mine` holds component pi of the product mod p (in [0, p), layout A) and
+// component 1 - pi has been written to xch for the partner warp.
+__device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane, int pi, const PrimeK &K, int ab,
+                                                 bool work, uint32_t &cseq, uint32_t (&mine)[32], uint32_t *tbuf,
+                                                 Producer &pr, bool producer)
 {
-    constexpr uint32_t P = Prime<PI>::p;
-    const uint32_t pinv = c_pinv_neg[PI];
-    const uint2 *twf = sm.tw[PI][0];
-    const uint2 *twi = sm.tw[PI][1];
+    const uint2 *twf = sm.tw[pi][0];
+    const uint2 *twi = sm.tw[pi][1];
     bool ok = true;
     uint32_t u[32];
     uint32_t x[32];
+    unsigned long long acc0[32], acc1[32];
 #pragma unroll
     for (int k = 0; k < 32; k++) {
-        acc0[k] = 0u;
-        acc1[k] = 0u;
+        acc0[k] = 0ull;
+        acc1[k] = 0ull;
     }
 #pragma unroll 1
     for (int c = 0; c < 2; c++) {
@@ -146,19 +147,21 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
         for (int p = 0; p < LG; p++) {
             const int sh = 22 - BGBIT * p;
             if (work) {
+                // digit + 512 in [0, 1024), shifted by p - 512 into [p - 512, p + 512) = digit mod p.
 #pragma unroll
-                for (int k = 0; k < 32; k++) x[k] = ((u[k] >> sh) & 1023u) + (P - 512u);
-                ntt_fwd<PI>(x, tbuf, twf, lane);
+                for (int k = 0; k < 32; k++) x[k] = ((u[k] >> sh) & 1023u) + (K.p - 512u);
+                ntt_fwd(x, tbuf, twf, lane, pi, K);
             }
             const uint32_t rs = cseq % BR_RING;
             const uint32_t par = (cseq / BR_RING) & 1u;
-            if (ok && !mbar_wait_bounded(&sm.full_bar[PI][rs], par, &sm.abort)) {
+            if (ok && !mbar_wait_bounded(&sm.full_bar[pi][rs], par, &sm.abort)) {
                 ok = false;
                 if (lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
             }
             if (work && ok) {
-                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[PI][rs]);
-                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[PI][rs] + RING_N);
+                // x in [0, 2p), key in [0, p): six products sum below 12 p^2 < 2^32 p.
+                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs]);
+                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs] + RING_N);
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const uint4 b0 = ch0[q * 32 + lane];
@@ -168,30 +171,34 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const int k = 4 * q + e;
-                        uint32_t t0 = acc0[k] + mont_mul<P>(x[k], bb0[e], pinv);
-                        acc0[k] = umin_u32(t0, t0 - 2u * P);
-                        uint32_t t1 = acc1[k] + mont_mul<P>(x[k], bb1[e], pinv);
-                        acc1[k] = umin_u32(t1, t1 - 2u * P);
+                        acc0[k] += (unsigned long long)x[k] * bb0[e];
+                        acc1[k] += (unsigned long long)x[k] * bb1[e];
                     }
                 }
             }
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(&sm.empty_bar[PI][rs]);
+                mbar_arrive(&sm.empty_bar[pi][rs]);
                 // Refill the slot released one chunk ago (BR_RING - 1 chunks of lookahead).
-                if (producer) produce<PI>(sm, pr, cseq + BR_RING);
+                if (producer) produce(sm, pr, cseq + BR_RING);
             }
             __syncwarp();
             cseq++;
         }
     }
     if (work && ok) {
-        ntt_inv<PI>(acc0, tbuf, twi, lane);
-        ntt_inv<PI>(acc1, tbuf, twi, lane);
+#pragma unroll 1
+        for (int c = 0; c < 2; c++) {
 #pragma unroll
-        for (int k = 0; k < 32; k++) {
-            acc0[k] = umin_u32(acc0[k], acc0[k] - P);
-            acc1[k] = umin_u32(acc1[k], acc1[k] - P);
+            for (int k = 0; k < 32; k++) x[k] = redc64(c == 0 ? acc0[k] : acc1[k], K);
+            ntt_inv(x, tbuf, twi, lane, pi, K);
+            if (c == pi) {
+#pragma unroll
+                for (int k = 0; k < 32; k++) mine[k] = umin_u32(x[k], x[k] - K.p);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; k++) sm.xch[slot][c][lane + 32 * k] = umin_u32(x[k], x[k] - K.p);
+            }
         }
     }
     return ok;
@@ -202,9 +209,9 @@ __device__ __forceinline__ uint32_t crt_lift(uint32_t x0, uint32_t x1)
     // V = x0 + p0 t, t = (x1 - x0) p0^-1 mod p1, V in [0, p0 p1); centred lift mod 2^32.
     constexpr uint64_t PP = (uint64_t)PRIME0 * (uint64_t)PRIME1;
     const uint2 inv = c_crt;
-    uint32_t x0r = umin_u32(x0, x0 - PRIME1);
-    uint32_t d = x1 - x0r + PRIME1;
-    uint32_t t = shoup_mul<PRIME1>(d, inv.x, inv.y);
+    const uint32_t x0r = umin_u32(x0, x0 - PRIME1);
+    const uint32_t d = x1 - x0r + PRIME1;
+    uint32_t t = shoup_mul_r(d, inv.x, inv.y, PRIME1);
     t = umin_u32(t, t - PRIME1);
     const uint64_t V = (uint64_t)PRIME0 * t + x0;
     uint32_t r = (uint32_t)V;
@@ -212,29 +219,31 @@ __device__ __forceinline__ uint32_t crt_lift(uint32_t x0, uint32_t x1)
     return r;
 }
 
-// Loop of one compute warp (prime PI) over its CTA's ciphertext groups.
-template <int PI>
+// Loop of one compute warp over its CTA's ciphertext groups.
 __device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int warp, int lane, int ngroups)
 {
     const int slot = warp >> 1;
+    const int pi = warp & 1;
     const int bar_id = 1 + slot;
     const int n = a.n;
+    const PrimeK K = prime_k(pi);
     uint32_t *tbuf = sm.tbuf[warp];
     uint32_t cseq = 0;
-    uint32_t acc0[32], acc1[32];
+    uint32_t mine[32];
     const bool producer = slot == 0 && lane == 0;
     Producer pr;
     pr.bsk_hat = a.bsk_hat;
     pr.n = n;
+    pr.pi = pi;
     pr.issued = 0;
-    const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     pr.total = (uint32_t)my_groups * (uint32_t)n * ROWS;
-    if (producer) produce<PI>(sm, pr, BR_RING);
+    if (producer) produce(sm, pr, BR_RING);
 
     for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int job = g * BR_SLOTS + slot;
         const bool active = job < a.jobs;
-        if (PI == 1 && active) {
+        if (pi == 1 && active) {
             const uint16_t *src = a.abar + (size_t)job * a.abar_stride;
             for (int i = lane; i <= n; i += 32) sm.abar[slot][i] = src[i];
             __syncwarp();
@@ -250,31 +259,28 @@ __device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int wa
         for (int i = 0; i < n && !aborted; i++) {
             const int ab = active ? (int)sm.abar[slot][i] : 0;
             const bool work = ab != 0;
-            const bool ok = external_product<PI>(sm, slot, lane, ab, work, cseq, acc0, acc1, tbuf, pr, producer);
-            if (PI == 0 && work && ok) {
-#pragma unroll
-                for (int k = 0; k < 32; k++) {
-                    sm.xch[slot][0][lane + 32 * k] = acc0[k];
-                    sm.xch[slot][1][lane + 32 * k] = acc1[k];
-                }
-            }
+            const bool ok = external_product(sm, slot, lane, pi, K, ab, work, cseq, mine, tbuf, pr, producer);
             aborted = bar_red_or(bar_id, 64, !ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
             if (aborted) break;
-            if (PI == 1 && work) {
+            if (work) {
+                // Component pi: residue mod p_pi in `mine`, the other prime's residue in xch.
+                uint32_t *A = sm.acc[slot][pi];
+                const uint32_t *X = sm.xch[slot][pi];
 #pragma unroll
                 for (int k = 0; k < 32; k++) {
                     const int j = lane + 32 * k;
-                    sm.acc[slot][0][j] += crt_lift(sm.xch[slot][0][j], acc0[k]);
-                    sm.acc[slot][1][j] += crt_lift(sm.xch[slot][1][j], acc1[k]);
+                    const uint32_t x0 = pi == 0 ? mine[k] : X[j];
+                    const uint32_t x1 = pi == 0 ? X[j] : mine[k];
+                    A[j] += crt_lift(x0, x1);
                 }
             }
             aborted = bar_red_or(bar_id, 64, false);
         }
         if (aborted) {
-            if (lane == 0 && PI == 1) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            if (lane == 0 && pi == 1) atomicOr(a.err, DEV_ERR_TIMEOUT);
             break;
         }
-        if (PI == 1 && active) {
+        if (pi == 1 && active) {
             // Sample extraction: a'_0 = A_0, a'_j = -A_{N-j}, b' = B_0.
             uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
             for (int j = lane; j < RING_N; j += 32)
@@ -283,7 +289,7 @@ __device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int wa
         }
     }
     // No bulk copy may still be in flight when the CTA exits.
-    if (producer && !drain<PI>(sm, pr)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    if (producer && !drain(sm, pr)) atomicOr(a.err, DEV_ERR_TIMEOUT);
 }
 
 __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
@@ -304,12 +310,8 @@ __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
         mbar_fence_init();
     }
     __syncthreads();
-
     const int ngroups = (a.jobs + BR_SLOTS - 1) / BR_SLOTS;
-
-    // ---------------- compute warps ----------------
-    if ((warp & 1) == 0) compute_warp<0>(sm, a, warp, lane, ngroups);
-    else compute_warp<1>(sm, a, warp, lane, ngroups);
+    compute_warp(sm, a, warp, lane, ngroups);
 }
 
 // ---------------------------------------------------------------------------------
@@ -324,7 +326,7 @@ struct ConvSmem {
 };
 
 __global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, uint32_t *bsk_hat, int n,
-                                                         const uint2 *tw_lane, uint2 scale0, uint2 scale1)
+                                                         const uint2 *tw_lane, uint32_t scale0, uint32_t scale1)
 {
     __shared__ ConvSmem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -337,25 +339,24 @@ __global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, ui
     for (long poly = (long)blockIdx.x * 8 + warp; poly < total; poly += (long)gridDim.x * 8) {
         const int c = (int)(poly % 2);
         const int r = (int)((poly / 2) % ROWS);
-        const int p = (int)((poly / (2 * ROWS)) % 2);
+        const int pi = (int)((poly / (2 * ROWS)) % 2);
         const long i = poly / (4 * ROWS);
         const uint32_t *src = bsk + ((i * ROWS + r) * 2 + c) * RING_N;
-        const uint32_t P = p == 0 ? PRIME0 : PRIME1;
+        const PrimeK K = prime_k(pi);
         uint32_t x[32];
 #pragma unroll
         for (int k = 0; k < 32; k++) {
             const int32_t v = (int32_t)src[lane + 32 * k];
-            int64_t m = (int64_t)v % (int64_t)P;
-            if (m < 0) m += P;
+            int64_t m = (int64_t)v % (int64_t)K.p;
+            if (m < 0) m += K.p;
             x[k] = (uint32_t)m;
         }
-        if (p == 0) ntt_fwd<0>(x, sm.tbuf[warp], sm.tw[0], lane);
-        else ntt_fwd<1>(x, sm.tbuf[warp], sm.tw[1], lane);
-        const uint2 sc = p == 0 ? scale0 : scale1;   // (N^-1 2^32 mod p, unused)
-        uint32_t *dst = bsk_hat + ((i * 2 + p) * ROWS + r) * CHUNK_WORDS + c * RING_N;
+        ntt_fwd(x, sm.tbuf[warp], sm.tw[pi], lane, pi, K);
+        const uint64_t sc = pi == 0 ? scale0 : scale1;   // N^-1 2^32 mod p
+        uint32_t *dst = bsk_hat + ((i * 2 + pi) * ROWS + r) * CHUNK_WORDS + c * RING_N;
 #pragma unroll
         for (int k = 0; k < 32; k++) {
-            const uint64_t y = (uint64_t)(x[k] % P) * sc.x % P;
+            const uint64_t y = (uint64_t)(x[k] % K.p) * sc % K.p;
             dst[(k >> 2) * 128 + lane * 4 + (k & 3)] = (uint32_t)y;
         }
     }
@@ -364,6 +365,27 @@ __global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, ui
 // ---------------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------------
+cudaError_t upload_constants(const NttTables &t)
+{
+    uint4 prm[2];
+    for (int pi = 0; pi < 2; pi++)
+        prm[pi] = make_uint4(t.prime[pi], 2u * t.prime[pi], t.pinv_neg[pi], t.red_one[pi]);
+    cudaError_t e = cudaMemcpyToSymbol(c_tw, t.ctw, sizeof(t.ctw));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_prm, prm, sizeof(prm));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_crt, &t.crt, sizeof(t.crt));
+    return e;
+}
+
+cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane,
+                              uint32_t scale0, uint32_t scale1, int num_sms, cudaStream_t st)
+{
+    const long polys = (long)n * 2 * ROWS * 2;
+    long grid = (polys + 7) / 8;
+    if (grid > 4L * num_sms) grid = 4L * num_sms;
+    bsk_to_ntt_kernel<<<(int)grid, 256, 0, st>>>(bsk, bsk_hat, n, tw_lane, scale0, scale1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
                       cudaStream_t st)
@@ -376,25 +398,6 @@ cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, cons
     const int groups = (jobs + BR_SLOTS - 1) / BR_SLOTS;
     const int grid = groups < num_sms ? groups : num_sms;
     br_kernel<<<grid, BR_THREADS, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t upload_constants(const NttTables &t)
-{
-    cudaError_t e = cudaMemcpyToSymbol(c_tw, t.ctw, sizeof(t.ctw));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pinv_neg, t.pinv_neg, sizeof(t.pinv_neg));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_crt, &t.crt, sizeof(t.crt));
-    return e;
-}
-
-cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane,
-                              uint32_t scale0, uint32_t scale1, int num_sms, cudaStream_t st)
-{
-    const long polys = (long)n * 2 * ROWS * 2;
-    long grid = (polys + 7) / 8;
-    if (grid > 4L * num_sms) grid = 4L * num_sms;
-    bsk_to_ntt_kernel<<<(int)grid, 256, 0, st>>>(bsk, bsk_hat, n, tw_lane, make_uint2(scale0, 0),
-                                                 make_uint2(scale1, 0));
     return cudaGetLastError();
 }
 

@@ -25,47 +25,18 @@ constexpr uint32_t GADGET_OFF = (512u << 22) + (512u << 12) + (512u << 2) + 2u;
 constexpr uint32_t T_EIGHTH = 0x20000000u;
 constexpr uint32_t T_QUARTER = 0x40000000u;
 
-// The two NTT primes (p = c 2^e + 1 with 2048 | p - 1 and 4p < 2^32, so that lazy
-// Harvey butterflies keep every value in [0, 4p)).  Their product (~2^59.8) exceeds
-// twice the largest |sum_r sum_j d b| = 6 * 1024 * 512 * 2^31 ~ 2^52.6 of one external
-// product, so the centred CRT lift recovers every coefficient exactly.
-constexpr uint32_t PRIME0 = 1004535809u;  // 479 * 2^21 + 1
-constexpr uint32_t PRIME1 = 998244353u;   // 119 * 2^23 + 1
-
-template <int PI>
-struct Prime;
-template <>
-struct Prime<0> {
-    static constexpr uint32_t p = PRIME0;
-};
-template <>
-struct Prime<1> {
-    static constexpr uint32_t p = PRIME1;
-};
+// The two NTT primes: p = c 2^11 + 1 (so Z_p holds a primitive 2048-th root of unity) and
+// 22 p < 2^32, so that a forward transform needs no reduction between its 10 stages (see
+// ntt.cuh).  Their product (~2^55.1) exceeds twice the largest |sum_r sum_j d b| =
+// 6 * 1024 * 512 * 2^31 ~ 2^52.6 of one external product (digits |d| <= 512, key words
+// centred in [-2^31, 2^31)), so the centred CRT lift recovers every coefficient exactly.
+constexpr uint32_t PRIME0 = 195198977u;  // 95312 * 2^11 + 1
+constexpr uint32_t PRIME1 = 195188737u;  // 95307 * 2^11 + 1
 
 // Number of per-lane twiddles of the five lane-dependent stages.
 constexpr int LANE_TW = 31;
 
 __device__ __forceinline__ uint32_t umin_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
-
-// Lazy Shoup product: for y < 2^32 and w < p, returns y w mod p in [0, 2p).
-template <uint32_t P>
-__device__ __forceinline__ uint32_t shoup_mul(uint32_t y, uint32_t w, uint32_t wp)
-{
-    uint32_t q = __umulhi(y, wp);
-    return y * w - q * P;
-}
-
-// Montgomery product a b 2^-32 mod p in [0, 2p) for a b < 2^32 p.
-template <uint32_t P>
-__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t pinv_neg)
-{
-    uint32_t lo = a * b;
-    uint32_t hi = __umulhi(a, b);
-    uint32_t m = lo * pinv_neg;
-    uint32_t mh = __umulhi(m, P);
-    return hi + mh + (lo != 0u ? 1u : 0u);
-}
 
 // ---------------------------------------------------------------------------------
 // PTX wrappers: mbarrier, bulk async copy, timers.

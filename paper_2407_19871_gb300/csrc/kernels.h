@@ -50,9 +50,11 @@ cudaError_t launch_keygen_ksk(int n, const uint8_t *s, const uint8_t *S, const u
 
 // Twiddle and constant tables (host side) uploaded at context creation.
 struct NttTables {
+    uint32_t prime[2];                  // the two NTT primes
     uint2 ctw[2][2][32];                // warp-uniform stages
     uint2 lane[2][2][31 * 32];          // lane-dependent stages
-    uint32_t pinv_neg[2];               // Montgomery constants
+    uint32_t pinv_neg[2];               // Montgomery constants -p^-1 mod 2^32
+    uint32_t red_one[2];                // floor(2^32 / p): lazy reduction by 1
     uint2 crt;                          // p0^-1 mod p1 and its Shoup companion
     uint32_t bsk_scale[2];              // N^-1 2^32 mod p
 };

@@ -79,8 +79,15 @@ void lp::build_ntt_tables(NttTables &t)
     const uint64_t primes[2] = {PRIME0, PRIME1};
     for (int pi = 0; pi < 2; pi++) {
         const uint64_t p = primes[pi];
-        // 3 generates the multiplicative group of both primes; psi has order 2N = 2048.
-        const uint64_t psi = powmod(3, (p - 1) / 2048, p);
+        t.prime[pi] = (uint32_t)p;
+        t.red_one[pi] = (uint32_t)((1ull << 32) / p);
+        // psi = g^((p-1)/2048) has order exactly 2048 iff psi^1024 = -1; take the first g
+        // that gives one.
+        uint64_t psi = 0;
+        for (uint64_t g = 2; g < 1000; g++) {
+            psi = powmod(g, (p - 1) / 2048, p);
+            if (powmod(psi, 1024, p) == p - 1) break;
+        }
         std::vector<uint64_t> zeta(RING_N), izeta(RING_N);
         for (uint32_t z = 0; z < (uint32_t)RING_N; z++) {
             zeta[z] = powmod(psi, bitrev10(z), p);

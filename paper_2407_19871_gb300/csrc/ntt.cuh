@@ -14,8 +14,13 @@
 // (layout B, transpose, layout A) with inverse twiddles, leaving natural order in layout A.
 // Its 1/N factor is folded into the transform-domain bootstrapping key.
 //
-// Values are kept lazily reduced (Harvey): forward inputs and outputs in [0, 4p), inverse
-// inputs and outputs in [0, 2p).
+// The prime is a runtime (warp-uniform) value, so both primes share one copy of the code.
+//
+// Value ranges.  Forward: no reduction inside the transform.  A Cooley-Tukey butterfly
+// maps (x, y) with x, y < B to x + t, x - t + 2p with t = y w mod p in [0, 2p) (lazy Shoup
+// product, valid for any y < 2^32), so the bound grows by 2p per stage: inputs in [0, 2p)
+// leave the 10 stages below 22p < 2^32 (p < 2^32 / 22), and one lazy Shoup reduction by 1
+// brings the output back to [0, 2p).  Inverse (Harvey): inputs and outputs in [0, 2p).
 #pragma once
 #include "common.cuh"
 
@@ -25,38 +30,49 @@ namespace lp {
 // as (w, floor(w 2^32 / p)); dir 0 = forward, 1 = inverse.  Only blind_rotate.cu includes
 // this header, so these constant-memory objects exist once.
 __constant__ uint2 c_tw[2][2][32];
-// Montgomery constants -p^-1 mod 2^32, per prime.
-__constant__ uint32_t c_pinv_neg[2];
+// Per prime: p, 2p, -p^-1 mod 2^32 (Montgomery), floor(2^32 / p) (reduction by 1).
+__constant__ uint4 c_prm[2];
 // CRT: p0^-1 mod p1 with its Shoup companion modulo p1.
 __constant__ uint2 c_crt;
 
-// Lane-twiddle table in shared memory: [LANE_TW][32] (w, w') per prime and direction;
-// slot q of stage s covers block (q - (2^(s-5) - 1)) of the lane's 16 / L blocks.
-template <int PI>
-__device__ __forceinline__ void bfly_fwd(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wp)
+struct PrimeK {
+    uint32_t p, p2, pinv_neg, rp;
+};
+
+__device__ __forceinline__ PrimeK prime_k(int pi)
 {
-    constexpr uint32_t P = Prime<PI>::p;
-    uint32_t X = umin_u32(x, x - 2u * P);
-    uint32_t T = shoup_mul<P>(y, w, wp);
-    x = X + T;
-    y = X - T + 2u * P;
+    const uint4 v = c_prm[pi];
+    return PrimeK{v.x, v.y, v.z, v.w};
 }
 
-template <int PI>
-__device__ __forceinline__ void bfly_inv(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wp)
+// Lazy Shoup product with a runtime modulus: y w mod p in [0, 2p) for any y < 2^32.
+__device__ __forceinline__ uint32_t shoup_mul_r(uint32_t y, uint32_t w, uint32_t wp, uint32_t p)
 {
-    constexpr uint32_t P = Prime<PI>::p;
-    uint32_t S = x + y;
-    S = umin_u32(S, S - 2u * P);
-    uint32_t D = x - y + 2u * P;
-    x = S;
-    y = shoup_mul<P>(D, w, wp);
+    return y * w - __umulhi(y, wp) * p;
+}
+
+__device__ __forceinline__ void bfly_fwd(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wp, const PrimeK &k)
+{
+    const uint32_t t = shoup_mul_r(y, w, wp, k.p);
+    y = x - t + k.p2;
+    x = x + t;
+}
+
+__device__ __forceinline__ void bfly_inv(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wp, const PrimeK &k)
+{
+    uint32_t s = x + y;
+    s = umin_u32(s, s - k.p2);
+    const uint32_t d = x - y + k.p2;
+    x = s;
+    y = shoup_mul_r(d, w, wp, k.p);
 }
 
 // tbuf: this warp's 32 x 33 word transpose buffer; tw: the lane table of this prime and
-// direction ([LANE_TW][32] uint2).
-template <int PI>
-__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane)
+// direction ([LANE_TW][32] (w, w')); slot base + b of stage s is block b of the lane's
+// 16 / L blocks (base = 2^(s-5) - 1).  Input in [0, 2p) (layout A), output in [0, 2p)
+// (layout B).
+__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane, int pi,
+                                        const PrimeK &K)
 {
 #pragma unroll
     for (int s = 0; s < 5; s++) {
@@ -64,8 +80,8 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const
 #pragma unroll
         for (int k = 0; k < 32; k++) {
             if (k & D) continue;
-            const uint2 z = c_tw[PI][0][(1 << s) + (k >> (5 - s))];
-            bfly_fwd<PI>(x[k], x[k + D], z.x, z.y);
+            const uint2 z = c_tw[pi][0][(1 << s) + (k >> (5 - s))];
+            bfly_fwd(x[k], x[k + D], z.x, z.y, K);
         }
     }
 #pragma unroll
@@ -84,14 +100,17 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const
 #pragma unroll
             for (int o = 0; o < L; o++) {
                 const int k = b * 2 * L + o;
-                bfly_fwd<PI>(x[k], x[k + L], z.x, z.y);
+                bfly_fwd(x[k], x[k + L], z.x, z.y, K);
             }
         }
     }
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] -= __umulhi(x[k], K.rp) * K.p;
 }
 
-template <int PI>
-__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane)
+// Input in [0, 2p) (layout B), output in [0, 2p) (layout A).
+__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane, int pi,
+                                        const PrimeK &K)
 {
 #pragma unroll
     for (int s = 9; s >= 5; s--) {
@@ -103,7 +122,7 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const
 #pragma unroll
             for (int o = 0; o < L; o++) {
                 const int k = b * 2 * L + o;
-                bfly_inv<PI>(x[k], x[k + L], z.x, z.y);
+                bfly_inv(x[k], x[k + L], z.x, z.y, K);
             }
         }
     }
@@ -119,10 +138,18 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const
 #pragma unroll
         for (int k = 0; k < 32; k++) {
             if (k & D) continue;
-            const uint2 z = c_tw[PI][1][(1 << s) + (k >> (5 - s))];
-            bfly_inv<PI>(x[k], x[k + D], z.x, z.y);
+            const uint2 z = c_tw[pi][1][(1 << s) + (k >> (5 - s))];
+            bfly_inv(x[k], x[k + D], z.x, z.y, K);
         }
     }
+}
+
+// Montgomery reduction of T < 2^32 p: T 2^-32 mod p in [0, 2p).
+__device__ __forceinline__ uint32_t redc64(unsigned long long T, const PrimeK &K)
+{
+    const uint32_t lo = (uint32_t)T, hi = (uint32_t)(T >> 32);
+    const uint32_t m = lo * K.pinv_neg;
+    return hi + __umulhi(m, K.p) + (lo != 0u ? 1u : 0u);
 }
 
 }  // namespace lp
