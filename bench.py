@@ -202,7 +202,7 @@ def run_gpu(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(local)
+    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(local, count=COUNT)
     out = torch.empty_like(a)
     st = torch.cuda.current_stream()
 
@@ -292,7 +292,7 @@ def run_gpu(args) -> None:
         "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "NAND gate bootstrapping: 65,536 independent gates per step (n=630, N=1024, k=1, "
+        "config": {"workload": f"NAND gate bootstrapping: {COUNT:,} independent gates per step (n=630, N=1024, k=1, "
                                "Bgbit=10, lg=3, basebit=2, t=8; keys seed 0, inputs seed 1)",
                    "global_batch": COUNT * world, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (2 x 165 MB per step)"},
@@ -316,6 +316,7 @@ def run_gpu(args) -> None:
 
 
 def main():
+    global COUNT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -323,7 +324,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--per-gate", type=int, default=16, help="gates timed one per launch (0: skip)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--count", type=int, default=COUNT,
+                    help="gates per step (default 65,536; smaller values are for profiling only)")
     args = ap.parse_args()
+    COUNT = args.count
     if args.impl == "reference":
         run_reference(args)
     else:

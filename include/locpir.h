@@ -50,7 +50,7 @@ extern "C" {
  * with lg levels, key-switch base 2^basebit with t digits.  The paper fixes n (Section 5,
  * TFHE Parameters: 630 for the 128-bit set, 540 for the 80-bit set) and defers the rest to
  * TFHE; this build supports N = 1024, k = 1, Bgbit = 10, lg = 3, basebit = 2, t = 8 and
- * any n in [1, 1023]. */
+ * any n in [1, 639]. */
 typedef struct lp_params {
     int n, N, k, Bgbit, lg, basebit, t;
 } lp_params;
@@ -101,7 +101,9 @@ int lp_load_bsk(lp_ctx *ctx, const uint32_t *bsk, size_t words);
 int lp_load_bsk_device(lp_ctx *ctx, const uint32_t *bsk_dev, size_t words, void *stream);
 
 /* Key-switching key, layout [N][t][2^basebit][n + 1] uint32: entry [i][j][v] is an LWE
- * sample of v S_i 2^(32 - basebit (j+1)) under s.  Entries with v = 0 are never read. */
+ * sample of v S_i 2^(32 - basebit (j+1)) under s.  Entries with v = 0 are never read.  The
+ * library keeps it as a table of digit-pair sums (16 rows per coefficient and pair of digits,
+ * about 166 MB at n = 630) built on the device at load. */
 int lp_load_ksk(lp_ctx *ctx, const uint32_t *ksk, size_t words);
 int lp_load_ksk_device(lp_ctx *ctx, const uint32_t *ksk_dev, size_t words, void *stream);
 

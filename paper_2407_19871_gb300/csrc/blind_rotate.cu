@@ -34,7 +34,7 @@
 namespace lp {
 
 constexpr int BR_SLOTS = 4;
-constexpr int BR_RING = 4;
+constexpr int BR_RING = 3;
 constexpr int BR_COMPUTE_WARPS = 2 * BR_SLOTS;
 constexpr int BR_THREADS = BR_COMPUTE_WARPS * 32;
 constexpr int CHUNK_WORDS = 2 * RING_N;                 // one (i, prime, row) chunk
@@ -42,7 +42,8 @@ constexpr uint32_t CHUNK_BYTES = CHUNK_WORDS * 4u;
 constexpr int ABAR_STRIDE_MAX = 1024;                    // u16 entries per job (>= n + 1)
 
 struct __align__(16) BrSmem {
-    uint32_t ring[2][BR_RING][CHUNK_WORDS];              // 64 KB
+    uint32_t ring[2][BR_RING][CHUNK_WORDS];              // 48 KB
+    uint32_t ubuf[BR_COMPUTE_WARPS][RING_N];             // 32 KB: rounded differences, per warp
     uint32_t acc[BR_SLOTS][2][RING_N];                   // 32 KB
     uint32_t xch[BR_SLOTS][2][RING_N];                   // 32 KB
     uint32_t tbuf[BR_COMPUTE_WARPS][32 * 33];            // 33 KB
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
     const uint2 *twf = sm.tw[pi][0];
     const uint2 *twi = sm.tw[pi][1];
     bool ok = true;
-    uint32_t u[32];
+    uint32_t *U = sm.ubuf[2 * slot + pi];
     uint32_t x[32];
     unsigned long long acc0[32], acc1[32];
 #pragma unroll
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
                 const int idx = (j - ab) & (2 * RING_N - 1);
                 uint32_t v = A[idx & (RING_N - 1)];
                 v = (idx & RING_N) ? (0u - v) : v;
-                u[k] = v - A[j] + GADGET_OFF;
+                U[j] = v - A[j] + GADGET_OFF;
             }
         }
 #pragma unroll 1
@@ -149,7 +150,7 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
             if (work) {
                 // digit + 512 in [0, 1024), shifted by p - 512 into [p - 512, p + 512) = digit mod p.
 #pragma unroll
-                for (int k = 0; k < 32; k++) x[k] = ((u[k] >> sh) & 1023u) + (K.p - 512u);
+                for (int k = 0; k < 32; k++) x[k] = ((U[lane + 32 * k] >> sh) & 1023u) + (K.p - 512u);
                 ntt_fwd(x, tbuf, twf, lane, pi, K);
             }
             const uint32_t rs = cseq % BR_RING;

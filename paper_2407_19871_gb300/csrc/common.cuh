@@ -17,7 +17,7 @@ constexpr int ROWS = 2 * LG;           // TRGSW rows (k + 1) lg
 constexpr int KS_T = 8;
 constexpr int KS_BASEBIT = 2;
 constexpr int KS_BASE = 1 << KS_BASEBIT;
-constexpr int MAX_LWE_N = 1023;
+constexpr int MAX_LWE_N = 639;        // key-switch rows of n + 1 words fit 640 words
 constexpr int EXT_STRIDE = 1028;       // words per extracted N-LWE row (N + 1, padded to 16 B)
 
 // Gadget offset: sum_p (Bg/2) 2^(32 - Bgbit p) + 2^(31 - Bgbit lg) (rounding + recentring).

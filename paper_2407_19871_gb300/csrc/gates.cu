@@ -1,4 +1,4 @@
-// Gate pre-combination + modulus switch, batched key switching, and the client-side
+// Gate pre-combination + modulus switch, small helpers, and the client-side
 // kernels (encryption, phase, key generation from given randomness).
 #include "common.cuh"
 #include "kernels.h"
@@ -80,113 +80,6 @@ __global__ void precomb_indexed_kernel(const BrJob *jobs, size_t njobs, const ui
             if (J.coef[k] != 0) x += (uint32_t)J.coef[k] * pool[(size_t)J.in[k] * (n + 1) + w];
         if (w == n) x += J.bconst;
         abar[jb * abar_stride + w] = modswitch_2048(x);
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// Key switching.  For an N-LWE (a', b'): out = (0, b') - sum_{i<N, j<t} KSK[i][j][v_ij],
-// v_ij = ((a'_i + 2^15) >> (30 - 2j)) & 3, skipping v = 0.  A CTA takes KS_CT outputs
-// and all n + 1 output words (KS_COLS per thread); every KSK row it reads serves KS_CT
-// ciphertexts.  MUX jobs sum their two extracted samples and (0, 1/8) while staging.
-// ---------------------------------------------------------------------------------
-constexpr int KS_CT = 16;
-constexpr int KS_THREADS = 128;
-constexpr int KS_COLS = 5;      // n + 1 <= 640
-constexpr int KS_ICHUNK = 64;
-
-__global__ void __launch_bounds__(KS_THREADS) ks_kernel(const uint32_t *ext, const KsJob *jobs, size_t njobs,
-                                                        int dense_mux, uint32_t *out, const uint32_t *ksk, int n)
-{
-    __shared__ uint32_t xs[KS_CT][KS_ICHUNK];
-    __shared__ uint32_t body[KS_CT];
-    __shared__ int srcs[KS_CT][2];
-    __shared__ int dsts[KS_CT];
-    const int tid = threadIdx.x;
-    const size_t first = (size_t)blockIdx.x * KS_CT;
-    if (tid < KS_CT) {
-        const size_t g = first + tid;
-        int e1 = -1, e2 = -1, o = -1;
-        uint32_t bc = 0u;
-        if (g < njobs) {
-            if (jobs) {
-                const KsJob J = jobs[g];
-                e1 = J.e1; e2 = J.e2; bc = J.bconst; o = J.out;
-            } else {
-                e1 = (int)g; o = (int)g;
-                if (dense_mux) { e2 = (int)(g + njobs); bc = T_EIGHTH; }
-            }
-            uint32_t bsum = ext[(size_t)e1 * EXT_STRIDE + RING_N] + bc;
-            if (e2 >= 0) bsum += ext[(size_t)e2 * EXT_STRIDE + RING_N];
-            body[tid] = bsum;
-        } else {
-            body[tid] = 0u;
-        }
-        srcs[tid][0] = e1; srcs[tid][1] = e2; dsts[tid] = o;
-    }
-    __syncthreads();
-
-    const int W = n + 1;
-    uint32_t acc[KS_CT][KS_COLS];
-#pragma unroll
-    for (int ct = 0; ct < KS_CT; ct++)
-#pragma unroll
-        for (int q = 0; q < KS_COLS; q++) acc[ct][q] = (tid + KS_THREADS * q == n) ? body[ct] : 0u;
-
-    for (int i0 = 0; i0 < RING_N; i0 += KS_ICHUNK) {
-        __syncthreads();
-        for (int e = tid; e < KS_CT * KS_ICHUNK; e += KS_THREADS) {
-            const int ct = e / KS_ICHUNK, ii = e % KS_ICHUNK;
-            const int e1 = srcs[ct][0], e2 = srcs[ct][1];
-            uint32_t v = 0u;
-            if (e1 >= 0) {
-                v = ext[(size_t)e1 * EXT_STRIDE + i0 + ii];
-                if (e2 >= 0) v += ext[(size_t)e2 * EXT_STRIDE + i0 + ii];
-            }
-            xs[ct][ii] = v + (1u << 15);
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int ii = 0; ii < KS_ICHUNK; ii++) {
-            const int i = i0 + ii;
-            uint32_t xv[KS_CT];
-#pragma unroll
-            for (int ct = 0; ct < KS_CT; ct++) xv[ct] = xs[ct][ii];
-#pragma unroll 2
-            for (int j = 0; j < KS_T; j++) {
-                const uint32_t *row = ksk + (size_t)((i * KS_T + j) * KS_BASE) * W;
-                uint32_t k1[KS_COLS], k2[KS_COLS], k3[KS_COLS];
-#pragma unroll
-                for (int q = 0; q < KS_COLS; q++) {
-                    const int col = tid + KS_THREADS * q;
-                    const bool ok = col < W;
-                    k1[q] = ok ? __ldg(row + W + col) : 0u;
-                    k2[q] = ok ? __ldg(row + 2 * W + col) : 0u;
-                    k3[q] = ok ? __ldg(row + 3 * W + col) : 0u;
-                }
-                const int sh = 30 - 2 * j;
-#pragma unroll
-                for (int ct = 0; ct < KS_CT; ct++) {
-                    const uint32_t v = (xv[ct] >> sh) & 3u;
-#pragma unroll
-                    for (int q = 0; q < KS_COLS; q++) {
-                        uint32_t s = v == 1u ? k1[q] : 0u;
-                        s = v == 2u ? k2[q] : s;
-                        s = v == 3u ? k3[q] : s;
-                        acc[ct][q] -= s;
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int ct = 0; ct < KS_CT; ct++) {
-        const int o = dsts[ct];
-        if (o < 0) continue;
-#pragma unroll
-        for (int q = 0; q < KS_COLS; q++) {
-            const int col = tid + KS_THREADS * q;
-            if (col < W) out[(size_t)o * W + col] = acc[ct][q];
-        }
     }
 }
 
@@ -350,15 +243,6 @@ cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32
     if (!njobs) return cudaSuccess;
     precomb_indexed_kernel<<<grid_for(njobs * (n + 1), 256, num_sms), 256, 0, st>>>(jobs, njobs, pool, n, abar,
                                                                                      abar_stride);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
-                      const uint32_t *ksk, int n, cudaStream_t st)
-{
-    if (!njobs) return cudaSuccess;
-    const size_t grid = (njobs + KS_CT - 1) / KS_CT;
-    ks_kernel<<<(unsigned)grid, KS_THREADS, 0, st>>>(ext, jobs, njobs, dense_mux, out, ksk, n);
     return cudaGetLastError();
 }
 

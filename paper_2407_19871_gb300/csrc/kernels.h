@@ -33,8 +33,11 @@ cudaError_t launch_modswitch(const uint32_t *lwe, int n, size_t jobs, uint16_t *
                              cudaStream_t st);
 cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32_t *pool, int n, uint16_t *abar,
                                    int abar_stride, int num_sms, cudaStream_t st);
+// Key switch from the digit-pair table T (built by launch_ks_table at key load).
 cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
-                      const uint32_t *ksk, int n, cudaStream_t st);
+                      const uint32_t *T, int n, int *err, int num_sms, cudaStream_t st);
+cudaError_t launch_ks_table(const uint32_t *ksk, uint32_t *T, int n, int num_sms, cudaStream_t st);
+__host__ __device__ size_t ks_table_words(int n);
 cudaError_t launch_negate(const uint32_t *in, uint32_t *out, size_t words, int num_sms, cudaStream_t st);
 cudaError_t launch_gather(const uint32_t *pool, const int *slots, const uint8_t *neg, size_t cnt, int n,
                           uint32_t *out, int num_sms, cudaStream_t st);

@@ -362,12 +362,25 @@ static int load_ksk_common(lp_ctx *c, const uint32_t *src, bool on_device, size_
     if (words != ksk_words(c->params))
         return fail(LP_EINVAL, "key-switching key has %zu words, expected %zu", words, ksk_words(c->params));
     cudaSetDevice(c->device);
-    int rc = ensure_buf(c->ksk, words * sizeof(uint32_t), "key-switching key");
+    // The context keeps only the digit-pair table the key switch reads (see keyswitch.cu).
+    int rc = ensure_buf(c->ksk, ks_table_words(c->params.n) * sizeof(uint32_t), "key-switching table");
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(c->ksk.ptr, src, words * 4,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    DevBuf staging;
+    const uint32_t *dsrc = src;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        rc = ensure_buf(staging, words * sizeof(uint32_t), "key-switching key staging");
+        if (rc) return rc;
+        e = cudaMemcpyAsync(staging.ptr, src, words * 4, cudaMemcpyHostToDevice, st);
+        dsrc = static_cast<const uint32_t *>(staging.ptr);
+    }
+    if (e == cudaSuccess) {
+        e = launch_ks_table(dsrc, static_cast<uint32_t *>(c->ksk.ptr), c->params.n, c->num_sms, st);
+        c->launches++;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "copy key-switching key");
+    free_buf(staging);
+    if (e != cudaSuccess) return cuda_fail(e, "build key-switching table");
     c->have_ksk = true;
     return LP_OK;
 }
@@ -413,7 +426,8 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
     cudaEvent_t ev0;
     timer_begin(c, "ks", st, &ev0);
     cudaError_t e = launch_ks(static_cast<const uint32_t *>(c->ext.ptr), jobs, njobs, dense_mux, out,
-                              static_cast<const uint32_t *>(c->ksk.ptr), c->params.n, st);
+                              static_cast<const uint32_t *>(c->ksk.ptr), c->params.n,
+                              static_cast<int *>(c->err.ptr), c->num_sms, st);
     timer_end(c, "ks", st, ev0);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "key switch launch");

@@ -94,7 +94,8 @@ extern "C" int lp_gate_batch_noalloc(lp_ctx *c, int op, const uint32_t *a, const
                   static_cast<int *>(c->err.ptr), c->num_sms, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
-    e = launch_ks(ext, nullptr, count, op == LP_MUX, out, static_cast<const uint32_t *>(c->ksk.ptr), n, st);
+    e = launch_ks(ext, nullptr, count, op == LP_MUX, out, static_cast<const uint32_t *>(c->ksk.ptr), n,
+                  static_cast<int *>(c->err.ptr), c->num_sms, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
     return LP_OK;
