@@ -107,6 +107,18 @@ int lp_load_bsk_device(lp_ctx *ctx, const uint32_t *bsk_dev, size_t words, void 
 int lp_load_ksk(lp_ctx *ctx, const uint32_t *ksk, size_t words);
 int lp_load_ksk_device(lp_ctx *ctx, const uint32_t *ksk_dev, size_t words, void *stream);
 
+/* Key files (the keys are the only persistent state; this is their checkpoint format):
+ * header "LPKEYS01", version, the 7 parameters, both word counts and the SHA-256 (FIPS 180-4) of
+ * the two key arrays, then the bootstrapping key and the key-switching key in the layouts above.
+ * lp_save_keys_file writes one from host arrays (no context).  lp_verify_keys_file checks a file
+ * without loading it (LP_ECORRUPT on a bad header, a short file or a checksum mismatch).
+ * lp_load_keys_file verifies and loads into a context whose parameters must match.
+ * lp_sha256: the hash itself (host). */
+int lp_save_keys_file(const lp_params *p, const uint32_t *bsk, const uint32_t *ksk, const char *path);
+int lp_verify_keys_file(const char *path, lp_params *params_out);
+int lp_load_keys_file(lp_ctx *ctx, const char *path);
+int lp_sha256(const void *data, size_t bytes, uint8_t out[32]);
+
 /* ---- gate bootstrapping ----------------------------------------------------------------
  * lp_gate_batch: count independent gates out[g] = op(a[g], b[g]) (MUX: a[g] ? b[g] : c[g];
  * NOT reads a only; c is read by MUX only and may be NULL otherwise).  All pointers device,
@@ -171,6 +183,48 @@ typedef struct lp_query {
 } lp_query;
 int lp_locpir_batch(lp_ctx *ctx, const lp_query *q, size_t nq, void *stream);
 
+/* Plans: lp_plan_locpir schedules a batch of queries once (levels, job records, a plan-owned
+ * pool and scratch) and captures the whole evaluation -- input copies from the queries' pointers,
+ * every level's pre-combination / blind-rotation / key-switch pass, output copies -- into one
+ * CUDA graph.  lp_plan_run replays it on a stream (asynchronous; the queries' pointers must stay
+ * valid while the plan exists, their contents may change between runs).  lp_plan_info reports the
+ * plan's blind rotations, key switches and kernels per run. */
+typedef struct lp_plan lp_plan;
+int lp_plan_locpir(lp_ctx *ctx, const lp_query *q, size_t nq, lp_plan **out);
+int lp_plan_run(lp_plan *plan, void *stream);
+int lp_plan_info(const lp_plan *plan, uint64_t *blind_rotations, uint64_t *key_switches, uint64_t *kernels);
+int lp_plan_destroy(lp_plan *plan);
+
+/* ---- query server (continuous batching) ---------------------------------------------------
+ * lp_server_start: start a server thread on the context.  Queries are admitted in arrival order
+ * while their circuit's ciphertexts ((wires) x (n + 1) x 4 B: inputs, gate outputs, one trivial
+ * constant) fit in a device pool of mem_budget bytes; admission copies the inputs into the pool,
+ * where they stay resident until the result is written.  Each scheduler tick evaluates the next
+ * bootstrap level of every admitted query as one shared batch (pre-combination, blind rotation,
+ * key switch), so queries of different shapes and depths share batches.  policy LP_SERVER_QUEUE
+ * keeps queries that do not fit waiting; LP_SERVER_REJECT refuses them with LP_EBUSY.  Scratch for
+ * the shared batches is allocated outside the budget.  Results are bit-identical to
+ * lp_locpir_query on the same query.  While a server runs, its context's other evaluation calls
+ * may still be used from other threads only on other contexts.
+ * lp_server_submit: the query's device pointers (inputs and out_service) must stay valid until the
+ * query is done; *ticket identifies it.  A query larger than the whole budget returns LP_EBUSY.
+ * lp_server_poll: *done = 1 once out_service holds the result.  lp_server_wait: block up to
+ * timeout_ms (LP_ETIMEOUT).  lp_server_stats: counters and latency percentiles of completed
+ * queries (submit -> result on the device).  lp_server_stop: finish the admitted queries, stop
+ * the thread, free the pool. */
+#define LP_SERVER_QUEUE 0
+#define LP_SERVER_REJECT 1
+typedef struct lp_stats {
+    uint64_t submitted, admitted, completed, rejected, waiting, active, ticks, bootstraps;
+    double p50_ms, p99_ms, mean_ms, elapsed_s, queries_per_s, bootstraps_per_s;
+} lp_stats;
+int lp_server_start(lp_ctx *ctx, size_t mem_budget, int policy);
+int lp_server_submit(lp_ctx *ctx, const lp_query *q, uint64_t *ticket);
+int lp_server_poll(lp_ctx *ctx, uint64_t ticket, int *done);
+int lp_server_wait(lp_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
+int lp_server_stats(lp_ctx *ctx, lp_stats *out);
+int lp_server_stop(lp_ctx *ctx);
+
 /* ---- client-side helpers on the device (no context) -------------------------------------
  * Encrypt (Section 2.2) and the zero-phase samples of Algorithm 1: out[g] = (a_g,
  * <a_g, s> + e_g + mu_g) with the caller's uniform masks mask [count][n], noise [count]
@@ -190,6 +244,14 @@ int lp_client_keygen_bsk(const lp_params *p, const uint8_t *s, const uint8_t *S,
 int lp_client_keygen_ksk(const lp_params *p, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
                          const uint32_t *noise, uint32_t *ksk, void *stream);
 
+/* Algorithm 1 (Preprocess): out[g] = zero[g] + (0, f(bits[g])), turning the client's zero-phase
+ * samples zero [count][n + 1] (b = <a, s> + e, sent with the public key) into encryptions of the
+ * service bits bits [count] (uint8, 0 or 1).  The paper's text says the samples encrypt "0";
+ * their printed form b = a K + e has phase 0, which is the reading used (adding f(1) = +1/8 or
+ * f(0) = -1/8 then gives a valid encryption).  Device pointers. */
+int lp_preprocess_services(int n, const uint32_t *zero, const uint8_t *bits, uint32_t *out, size_t count,
+                           void *stream);
+
 /* ---- introspection -------------------------------------------------------------------- */
 /* Kernel launches this context has issued since creation (every launch of the library's
  * own kernels counts one). */
@@ -200,6 +262,12 @@ uint64_t lp_launch_count(const lp_ctx *ctx);
 int lp_set_timing(lp_ctx *ctx, int enable);
 int lp_kernel_time(lp_ctx *ctx, const char *kernel, double *ms_total, uint64_t *launches);
 int lp_reset_timing(lp_ctx *ctx);
+
+/* Failure-detection self-test: launches a kernel that waits on a barrier nothing completes,
+ * with the library's bounded wait (limit_ms, 1..10000).  The wait gives up, the kernel records
+ * a timeout and returns; the next lp_sync reports LP_ETIMEOUT and the context stays usable.
+ * Every wait inside the library's kernels uses the same bounded routine (2 s limit). */
+int lp_selftest_wait_timeout(lp_ctx *ctx, uint32_t limit_ms, void *stream);
 
 #ifdef __cplusplus
 }

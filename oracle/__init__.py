@@ -187,6 +187,20 @@ def encrypt(s: np.ndarray, bits, draws: LweDraws) -> np.ndarray:
     return encrypt_mu(s, encode(np.atleast_1d(bits)), draws)
 
 
+def zero_samples(s: np.ndarray, draws: LweDraws) -> np.ndarray:
+    """Zero-phase samples (a, <a, s> + e) the client sends with its public key (Algorithm 1's
+    inputs: b = a K + e)."""
+    return encrypt_mu(s, np.zeros(draws.mask.shape[0], np.uint32), draws)
+
+
+def preprocess(zero: np.ndarray, bits) -> np.ndarray:
+    """Algorithm 1 (Preprocess): S_i[j] + ct_ij, i.e. add the plaintext encoding (0, f(bit))
+    of each service bit to the client's zero-phase sample."""
+    out = _u32(np.atleast_2d(zero)).copy()
+    out[:, -1] = (out[:, -1].astype(np.uint64) + encode(np.atleast_1d(bits)).astype(np.uint64)) & 0xFFFFFFFF
+    return out
+
+
 def trivial(bit: int, n: int) -> np.ndarray:
     """Noiseless, maskless sample (0, f(bit))."""
     c = np.zeros(n + 1, np.uint32)

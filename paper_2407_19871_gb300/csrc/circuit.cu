@@ -10,124 +10,12 @@
 #include <cstring>
 #include <vector>
 
+#include "circuit.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "runtime.h"
 
 namespace lp {
-
-struct Sig {
-    int32_t w = -1;
-    bool neg = false;
-};
-
-struct Node {
-    int op;
-    Sig in[3];
-    int32_t out;
-};
-
-struct Circuit {
-    std::vector<int> depth;   // per wire
-    std::vector<Node> nodes;
-    int zero_w = -1;
-
-    int wire(int d)
-    {
-        depth.push_back(d);
-        return (int)depth.size() - 1;
-    }
-    // k consecutive input wires.
-    int inputs(int k)
-    {
-        const int first = (int)depth.size();
-        for (int i = 0; i < k; i++) wire(0);
-        return first;
-    }
-    Sig zero()
-    {
-        if (zero_w < 0) zero_w = wire(0);
-        return Sig{zero_w, false};
-    }
-    static Sig NOT(Sig a) { return Sig{a.w, !a.neg}; }
-    Sig gate(int op, Sig a, Sig b, Sig c = Sig{})
-    {
-        int d = std::max(depth[a.w], depth[b.w]);
-        if (op == LP_MUX) d = std::max(d, depth[c.w]);
-        const int w = wire(d + 1);
-        Node nd;
-        nd.op = op;
-        nd.in[0] = a;
-        nd.in[1] = b;
-        nd.in[2] = c;
-        nd.out = w;
-        nodes.push_back(nd);
-        return Sig{w, false};
-    }
-};
-
-// HomCompS (Algorithm 2): t0 = Enc(0); with is_signed, both MSBs are flipped (lines 2-3);
-// for i = 0 .. l-1 (LSB first): t1 = XNOR(c1[i], c2[i]); t0 = MUX(t1, t0, c2[i]).
-static Sig comp_s(Circuit &C, int c1, int c2, int l, bool is_signed)
-{
-    Sig t0 = C.zero();
-    for (int i = 0; i < l; i++) {
-        Sig a{c1 + i, false}, b{c2 + i, false};
-        if (is_signed && i == l - 1) {
-            a = Circuit::NOT(a);
-            b = Circuit::NOT(b);
-        }
-        Sig t1 = C.gate(LP_XNOR, a, b);
-        t0 = C.gate(LP_MUX, t1, t0, b);
-    }
-    return t0;
-}
-
-// HomCompLE(a, b) = a <= b = NOT HomCompS(b, a).
-static Sig comp_le(Circuit &C, int a, int b, int l, bool is_signed)
-{
-    return Circuit::NOT(comp_s(C, b, a, l, is_signed));
-}
-
-// LocPIR (Algorithm 3) for one query; x, y, boxes, services are first input wires.
-static std::vector<Sig> build_locpir(Circuit &C, int l, bool is_signed, int x, int y, int n_boxes, int boxes, int m,
-                                     int services, int comb)
-{
-    std::vector<std::vector<Sig>> rows;
-    rows.reserve(n_boxes);
-    for (int i = 0; i < n_boxes; i++) {
-        const int X1 = boxes + (4 * i + 0) * l, X2 = boxes + (4 * i + 1) * l;
-        const int Y1 = boxes + (4 * i + 2) * l, Y2 = boxes + (4 * i + 3) * l;
-        Sig xl = comp_le(C, X1, x, l, is_signed);
-        Sig xr = comp_s(C, x, X2, l, is_signed);
-        Sig yl = comp_le(C, Y1, y, l, is_signed);
-        Sig yr = comp_s(C, y, Y2, l, is_signed);
-        Sig v1 = C.gate(LP_AND, xl, xr);
-        Sig v2 = C.gate(LP_AND, yl, yr);
-        Sig f = C.gate(LP_AND, v1, v2);
-        std::vector<Sig> Si(m);
-        for (int j = 0; j < m; j++) Si[j] = C.gate(LP_AND, f, Sig{services + i * m + j, false});  // Algorithm 5
-        rows.push_back(std::move(Si));
-    }
-    if (comb == LP_XOR_CHAIN) {  // Algorithm 4 as printed (its S_i[j] target read as S[j])
-        std::vector<Sig> S(m, C.zero());
-        for (auto &Si : rows)
-            for (int j = 0; j < m; j++) S[j] = C.gate(LP_XOR, S[j], Si[j]);
-        return S;
-    }
-    const int op = comb == LP_OR_TREE ? LP_OR : LP_XOR;
-    while (rows.size() > 1) {
-        std::vector<std::vector<Sig>> next;
-        for (size_t i = 0; i + 1 < rows.size(); i += 2) {
-            std::vector<Sig> r(m);
-            for (int j = 0; j < m; j++) r[j] = C.gate(op, rows[i][j], rows[i + 1][j]);
-            next.push_back(std::move(r));
-        }
-        if (rows.size() % 2) next.push_back(std::move(rows.back()));
-        rows.swap(next);
-    }
-    return rows[0];
-}
 
 // ---------------------------------------------------------------------------------
 // Execution.
@@ -141,13 +29,6 @@ struct OutputCopy {
     Sig sig;
     uint32_t *dst;
 };
-struct CopyEntry {
-    const uint32_t *src;
-    uint32_t *dst;
-    int32_t neg;
-    int32_t pad;
-};
-
 __global__ void copy_entries_kernel(const CopyEntry *e, size_t cnt, int n)
 {
     const int lane = threadIdx.x & 31;
@@ -161,136 +42,153 @@ __global__ void copy_entries_kernel(const CopyEntry *e, size_t cnt, int n)
     }
 }
 
-static void gate_base(int op, uint32_t &cst, int &ca, int &cb)
-{
-    switch (op) {
-    case LP_AND: cst = 0u - T_EIGHTH; ca = 1; cb = 1; break;
-    case LP_NAND: cst = T_EIGHTH; ca = -1; cb = -1; break;
-    case LP_OR: cst = T_EIGHTH; ca = 1; cb = 1; break;
-    case LP_XOR: cst = T_QUARTER; ca = 2; cb = 2; break;
-    default: cst = 0u - T_QUARTER; ca = -2; cb = -2; break;  // XNOR
-    }
-}
-
 struct Pass {
     size_t br_off, br_cnt, ks_off, ks_cnt;
 };
+
+// A levelled schedule: job records of every pass, in bootstrap-level order, plus the copies
+// in and out of the ciphertext pool.  Pool addresses in `outc` are offsets (in words) until
+// the pool is known.
+struct Schedule {
+    std::vector<BrJob> br;
+    std::vector<KsJob> ks;
+    std::vector<Pass> passes;
+    std::vector<CopyEntry> outc;
+    std::vector<InputCopy> ins;
+    size_t max_pass = 1, nwires = 0, br_bytes = 0, ks_bytes = 0, out_off = 0, job_bytes = 0;
+    int zero_w = -1;
+};
+
+static void schedule(const Circuit &C, const std::vector<InputCopy> &ins, const std::vector<OutputCopy> &outs, int n,
+                     Schedule &S)
+{
+    const size_t W = (size_t)n + 1;
+    const std::vector<std::vector<int>> levels = levels_of(C);
+    const int maxd = (int)levels.size() - 1;
+    const size_t MAXJ = 131072;
+    for (int d = 1; d <= maxd; d++) {
+        Pass ps{S.br.size(), 0, S.ks.size(), 0};
+        for (int idx : levels[d]) {
+            const Node &nd = C.nodes[idx];
+            const size_t need = nd.op == LP_MUX ? 2 : 1;
+            if (ps.br_cnt + need > MAXJ) {
+                S.passes.push_back(ps);
+                S.max_pass = std::max(S.max_pass, ps.br_cnt);
+                ps = Pass{S.br.size(), 0, S.ks.size(), 0};
+            }
+            append_gate_jobs(nd, 0, ps.br_cnt, S.br, S.ks);
+            ps.br_cnt += need;
+            ps.ks_cnt += 1;
+        }
+        if (ps.ks_cnt) {
+            S.passes.push_back(ps);
+            S.max_pass = std::max(S.max_pass, ps.br_cnt);
+        }
+    }
+    for (const OutputCopy &o : outs)
+        S.outc.push_back(CopyEntry{reinterpret_cast<const uint32_t *>((size_t)o.sig.w * W), o.dst, o.sig.neg ? 1 : 0, 0});
+    S.ins = ins;
+    S.zero_w = C.zero_w;
+    S.nwires = C.depth.size();
+    S.br_bytes = S.br.size() * sizeof(BrJob);
+    S.ks_bytes = S.ks.size() * sizeof(KsJob);
+    S.out_off = (S.br_bytes + S.ks_bytes + 255) & ~(size_t)255;
+    S.job_bytes = S.out_off + S.outc.size() * sizeof(CopyEntry) + 256;
+}
+
+// Buffers a schedule runs on.
+struct RunBufs {
+    uint32_t *pool;
+    char *jobs;
+    uint16_t *abar;
+    uint32_t *ext;
+};
+
+// Upload the job records (host -> device, on st).
+static cudaError_t upload_schedule(Schedule &S, const RunBufs &B, cudaStream_t st)
+{
+    for (CopyEntry &e : S.outc)
+        e.src = B.pool + reinterpret_cast<size_t>(e.src);   // offsets -> pool addresses
+    cudaError_t e = cudaSuccess;
+    if (S.br_bytes) e = cudaMemcpyAsync(B.jobs, S.br.data(), S.br_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && S.ks_bytes)
+        e = cudaMemcpyAsync(B.jobs + S.br_bytes, S.ks.data(), S.ks_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !S.outc.empty())
+        e = cudaMemcpyAsync(B.jobs + S.out_off, S.outc.data(), S.outc.size() * sizeof(CopyEntry),
+                            cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// Enqueue the whole evaluation: inputs into the pool, every level's passes, outputs out.
+// Only stream-ordered work: the same sequence is captured into a CUDA graph by plans.
+static int enqueue_schedule(lp_ctx *c, const Schedule &S, const RunBufs &B, cudaStream_t st, bool timed)
+{
+    const int n = c->params.n;
+    const size_t W = (size_t)n + 1;
+    cudaError_t e = cudaSuccess;
+    for (const InputCopy &in : S.ins) {
+        e = cudaMemcpyAsync(B.pool + (size_t)in.first_wire * W, in.src, (size_t)in.count * W * 4,
+                            cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "circuit input copy");
+    }
+    if (S.zero_w >= 0) {
+        e = launch_trivial(B.pool + (size_t)S.zero_w * W, n, 0u - T_EIGHTH, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "trivial constant");
+    }
+    const BrJob *dbr = reinterpret_cast<const BrJob *>(B.jobs);
+    const KsJob *dks = reinterpret_cast<const KsJob *>(B.jobs + S.br_bytes);
+    int *err = static_cast<int *>(c->err.ptr);
+    for (const Pass &ps : S.passes) {
+        e = launch_precomb_indexed(dbr + ps.br_off, ps.br_cnt, B.pool, n, B.abar, abar_stride(c), c->num_sms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
+        cudaEvent_t ev0 = nullptr;
+        if (timed) timer_begin(c, "br", st, &ev0);
+        e = launch_br(B.abar, abar_stride(c), B.ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                      static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)ps.br_cnt, T_EIGHTH, err, c->num_sms, st);
+        if (timed) timer_end(c, "br", st, ev0);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
+        if (timed) timer_begin(c, "ks", st, &ev0);
+        e = launch_ks(B.ext, dks + ps.ks_off, ps.ks_cnt, 0, B.pool, static_cast<const uint32_t *>(c->ksk.ptr), n, err,
+                      c->num_sms, st);
+        if (timed) timer_end(c, "ks", st, ev0);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
+    }
+    if (!S.outc.empty()) {
+        e = launch_copy_entries(reinterpret_cast<const CopyEntry *>(B.jobs + S.out_off), S.outc.size(), n, c->num_sms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "output copy launch");
+    }
+    return LP_OK;
+}
 
 static int execute(lp_ctx *c, const Circuit &C, const std::vector<InputCopy> &ins, const std::vector<OutputCopy> &outs,
                    cudaStream_t st)
 {
     const int n = c->params.n;
     const size_t W = (size_t)n + 1;
-    const size_t nw = C.depth.size();
-    int rc = ensure_buf(c->pool, nw * W * 4, "ciphertext pool");
+    Schedule S;
+    schedule(C, ins, outs, n, S);
+    int rc = ensure_buf(c->pool, S.nwires * W * 4, "ciphertext pool");
+    if (!rc) rc = ensure_buf(c->jobs, S.job_bytes, "job records");
+    if (!rc) rc = ensure_scratch(c, S.max_pass);
     if (rc) return rc;
-    uint32_t *pool = static_cast<uint32_t *>(c->pool.ptr);
+    RunBufs B{static_cast<uint32_t *>(c->pool.ptr), static_cast<char *>(c->jobs.ptr),
+              static_cast<uint16_t *>(c->abar.ptr), static_cast<uint32_t *>(c->ext.ptr)};
+    cudaError_t e = upload_schedule(S, B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload job records");
+    return enqueue_schedule(c, S, B, st, c->timing);
+}
 
-    // Levels: nodes grouped by the bootstrap depth of their output, in creation order.
-    int maxd = 0;
-    for (const Node &nd : C.nodes) maxd = std::max(maxd, C.depth[nd.out]);
-    std::vector<std::vector<int>> levels(maxd + 1);
-    for (size_t i = 0; i < C.nodes.size(); i++) levels[C.depth[C.nodes[i].out]].push_back((int)i);
-
-    const size_t MAXJ = 131072;
-    std::vector<BrJob> br;
-    std::vector<KsJob> ks;
-    std::vector<Pass> passes;
-    size_t max_pass = 1;
-    for (int d = 1; d <= maxd; d++) {
-        Pass ps{br.size(), 0, ks.size(), 0};
-        for (int idx : levels[d]) {
-            const Node &nd = C.nodes[idx];
-            const size_t need = nd.op == LP_MUX ? 2 : 1;
-            if (ps.br_cnt + need > MAXJ) {
-                passes.push_back(ps);
-                max_pass = std::max(max_pass, ps.br_cnt);
-                ps = Pass{br.size(), 0, ks.size(), 0};
-            }
-            auto sgn = [](const Sig &s, int coef) { return s.neg ? -coef : coef; };
-            KsJob kj;
-            kj.out = nd.out;
-            kj.e1 = (int)ps.br_cnt;
-            if (nd.op == LP_MUX) {
-                BrJob j1{}, j2{};
-                j1.in[0] = nd.in[0].w; j1.coef[0] = sgn(nd.in[0], 1);
-                j1.in[1] = nd.in[1].w; j1.coef[1] = sgn(nd.in[1], 1);
-                j1.in[2] = 0;          j1.coef[2] = 0;
-                j1.bconst = 0u - T_EIGHTH;
-                j2.in[0] = nd.in[0].w; j2.coef[0] = sgn(nd.in[0], -1);
-                j2.in[1] = nd.in[2].w; j2.coef[1] = sgn(nd.in[2], 1);
-                j2.in[2] = 0;          j2.coef[2] = 0;
-                j2.bconst = 0u - T_EIGHTH;
-                br.push_back(j1);
-                br.push_back(j2);
-                kj.e2 = (int)ps.br_cnt + 1;
-                kj.bconst = T_EIGHTH;
-            } else {
-                uint32_t cst; int ca, cb;
-                gate_base(nd.op, cst, ca, cb);
-                BrJob j{};
-                j.in[0] = nd.in[0].w; j.coef[0] = sgn(nd.in[0], ca);
-                j.in[1] = nd.in[1].w; j.coef[1] = sgn(nd.in[1], cb);
-                j.in[2] = 0;          j.coef[2] = 0;
-                j.bconst = cst;
-                br.push_back(j);
-                kj.e2 = -1;
-                kj.bconst = 0u;
-            }
-            ks.push_back(kj);
-            ps.br_cnt += need;
-            ps.ks_cnt += 1;
-        }
-        if (ps.ks_cnt) {
-            passes.push_back(ps);
-            max_pass = std::max(max_pass, ps.br_cnt);
-        }
-    }
-
-    std::vector<CopyEntry> outc;
-    outc.reserve(outs.size());
-    for (const OutputCopy &o : outs) outc.push_back(CopyEntry{pool + (size_t)o.sig.w * W, o.dst, o.sig.neg ? 1 : 0, 0});
-
-    const size_t br_bytes = br.size() * sizeof(BrJob), ks_bytes = ks.size() * sizeof(KsJob);
-    const size_t out_off = (br_bytes + ks_bytes + 255) & ~(size_t)255;
-    rc = ensure_buf(c->jobs, out_off + outc.size() * sizeof(CopyEntry) + 256, "job records");
-    if (!rc) rc = ensure_scratch(c, max_pass);
-    if (rc) return rc;
-    char *jb = static_cast<char *>(c->jobs.ptr);
-    cudaError_t e = cudaSuccess;
-    if (br_bytes) e = cudaMemcpyAsync(jb, br.data(), br_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && ks_bytes) e = cudaMemcpyAsync(jb + br_bytes, ks.data(), ks_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !outc.empty())
-        e = cudaMemcpyAsync(jb + out_off, outc.data(), outc.size() * sizeof(CopyEntry), cudaMemcpyHostToDevice, st);
-    for (const InputCopy &in : ins) {
-        if (e != cudaSuccess) break;
-        e = cudaMemcpyAsync(pool + (size_t)in.first_wire * W, in.src, (size_t)in.count * W * 4,
-                            cudaMemcpyDeviceToDevice, st);
-    }
-    if (e == cudaSuccess && C.zero_w >= 0) {
-        e = launch_trivial(pool + (size_t)C.zero_w * W, n, 0u - T_EIGHTH, st);
-        c->launches++;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "circuit setup");
-
-    const BrJob *dbr = reinterpret_cast<const BrJob *>(jb);
-    const KsJob *dks = reinterpret_cast<const KsJob *>(jb + br_bytes);
-    for (const Pass &ps : passes) {
-        e = launch_precomb_indexed(dbr + ps.br_off, ps.br_cnt, pool, n, static_cast<uint16_t *>(c->abar.ptr),
-                                   abar_stride(c), c->num_sms, st);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
-        if ((rc = run_br(c, ps.br_cnt, T_EIGHTH, st))) return rc;
-        if ((rc = run_ks(c, dks + ps.ks_off, ps.ks_cnt, 0, pool, st))) return rc;
-    }
-    if (!outc.empty()) {
-        int grid = (int)std::min<size_t>((outc.size() + 7) / 8, (size_t)c->num_sms * 16);
-        copy_entries_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const CopyEntry *>(jb + out_off), outc.size(), n);
-        c->launches++;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "output copy launch");
-    }
-    return LP_OK;
+cudaError_t launch_copy_entries(const CopyEntry *e, size_t cnt, int n, int num_sms, cudaStream_t st)
+{
+    if (!cnt) return cudaSuccess;
+    const int grid = (int)std::min<size_t>((cnt + 7) / 8, (size_t)num_sms * 16);
+    copy_entries_kernel<<<grid, 256, 0, st>>>(e, cnt, n);
+    return cudaGetLastError();
 }
 
 }  // namespace lp
@@ -330,7 +228,7 @@ extern "C" int lp_compare_batch(lp_ctx *c, int kind, int is_signed, int l, const
     return execute(c, C, ins, outs, static_cast<cudaStream_t>(stream));
 }
 
-static int check_query(const lp_query &q)
+int lp::check_query(const lp_query &q)
 {
     if (q.l < 1 || q.l > 64) return fail(LP_EINVAL, "bit width l=%d outside [1, 64]", q.l);
     if (q.n_boxes < 1) return fail(LP_EINVAL, "n_boxes=%d < 1", q.n_boxes);
@@ -372,4 +270,128 @@ extern "C" int lp_locpir_query(lp_ctx *c, int l, int is_signed, const uint32_t *
 {
     lp_query q{l, is_signed, n_boxes, m, comb, x, y, boxes, services, out_service};
     return lp_locpir_batch(c, &q, 1, stream);
+}
+
+// ---------------------------------------------------------------------------------
+// Plans: a LocPIR batch scheduled once and captured into a CUDA graph.
+// ---------------------------------------------------------------------------------
+struct lp_plan {
+    lp_ctx *c = nullptr;
+    Schedule S;
+    DevBuf pool, jobs, abar, ext;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0, blind_rotations = 0, key_switches = 0;
+};
+
+static void plan_free(lp_plan *P)
+{
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    for (DevBuf *b : {&P->pool, &P->jobs, &P->abar, &P->ext}) free_buf(*b);
+    delete P;
+}
+
+extern "C" int lp_plan_locpir(lp_ctx *c, const lp_query *q, size_t nq, lp_plan **out)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!q || !out || nq == 0) return fail(LP_EINVAL, "empty or null query list");
+    *out = nullptr;
+    const int n = c->params.n;
+    const size_t W = (size_t)n + 1;
+    Circuit C;
+    std::vector<InputCopy> ins;
+    std::vector<OutputCopy> outs;
+    for (size_t i = 0; i < nq; i++) {
+        if ((rc = check_query(q[i]))) return rc;
+        const lp_query &Q = q[i];
+        const int x = C.inputs(Q.l), y = C.inputs(Q.l);
+        const int bx = C.inputs(4 * Q.l * Q.n_boxes);
+        const int sv = C.inputs(Q.m * Q.n_boxes);
+        ins.push_back(InputCopy{x, Q.x, Q.l});
+        ins.push_back(InputCopy{y, Q.y, Q.l});
+        ins.push_back(InputCopy{bx, Q.boxes, 4 * Q.l * Q.n_boxes});
+        ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
+        std::vector<Sig> Sv = build_locpir(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, bx, Q.m, sv, Q.comb);
+        for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{Sv[j], Q.out_service + (size_t)j * W});
+    }
+    lp_plan *P = new lp_plan();
+    P->c = c;
+    schedule(C, ins, outs, n, P->S);
+    for (const Pass &ps : P->S.passes) {
+        P->blind_rotations += ps.br_cnt;
+        P->key_switches += ps.ks_cnt;
+    }
+    rc = ensure_buf(P->pool, P->S.nwires * W * 4, "plan pool");
+    if (!rc) rc = ensure_buf(P->jobs, P->S.job_bytes, "plan job records");
+    if (!rc) rc = ensure_buf(P->abar, P->S.max_pass * abar_stride(c) * sizeof(uint16_t), "plan scratch");
+    if (!rc) rc = ensure_buf(P->ext, P->S.max_pass * EXT_STRIDE * sizeof(uint32_t), "plan scratch");
+    if (rc) {
+        plan_free(P);
+        return rc;
+    }
+    RunBufs B{static_cast<uint32_t *>(P->pool.ptr), static_cast<char *>(P->jobs.ptr),
+              static_cast<uint16_t *>(P->abar.ptr), static_cast<uint32_t *>(P->ext.ptr)};
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = upload_schedule(P->S, B, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        plan_free(P);
+        return cuda_fail(e, "plan setup");
+    }
+    const uint64_t l0 = c->launches;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = enqueue_schedule(c, P->S, B, st, false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        P->graph = g;
+        if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "end graph capture");
+    } else {
+        rc = cuda_fail(e, "begin graph capture");
+    }
+    P->kernels = c->launches - l0;
+    c->launches = l0;
+    if (!rc) {
+        e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "instantiate graph");
+    }
+    cudaStreamDestroy(st);
+    if (rc) {
+        plan_free(P);
+        return rc;
+    }
+    *out = P;
+    return LP_OK;
+}
+
+extern "C" int lp_plan_run(lp_plan *P, void *stream)
+{
+    if (!P) return fail(LP_EINVAL, "null plan");
+    cudaSetDevice(P->c->device);
+    cudaError_t e = cudaGraphLaunch(P->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    P->c->launches += P->kernels;
+    return LP_OK;
+}
+
+extern "C" int lp_plan_info(const lp_plan *P, uint64_t *blind_rotations, uint64_t *key_switches, uint64_t *kernels)
+{
+    if (!P) return fail(LP_EINVAL, "null plan");
+    if (blind_rotations) *blind_rotations = P->blind_rotations;
+    if (key_switches) *key_switches = P->key_switches;
+    if (kernels) *kernels = P->kernels;
+    return LP_OK;
+}
+
+extern "C" int lp_plan_destroy(lp_plan *P)
+{
+    if (!P) return LP_OK;
+    cudaSetDevice(P->c->device);
+    cudaDeviceSynchronize();
+    plan_free(P);
+    return LP_OK;
 }

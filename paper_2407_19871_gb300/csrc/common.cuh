@@ -91,9 +91,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // Every wait in this library gives up after this long and reports LP_ETIMEOUT.
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
-// Bounded wait for the phase of the given parity; returns false on timeout or when
+// Bounded wait for the phase of the given parity; returns false after limit_ns or when
 // *abort (a CTA-wide flag in shared memory) is raised by another warp.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                                  uint64_t limit_ns = WAIT_LIMIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     uint64_t t0 = global_timer_ns();
@@ -101,7 +102,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*abort) return false;
-            if (global_timer_ns() - t0 > WAIT_LIMIT_NS) return false;
+            if (global_timer_ns() - t0 > limit_ns) return false;
         }
     }
 }

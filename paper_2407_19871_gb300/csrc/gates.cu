@@ -211,6 +211,39 @@ __global__ void keygen_ksk_kernel(int n, const uint8_t *s, const uint8_t *S, con
 }
 
 // ---------------------------------------------------------------------------------
+// Failure-detection self-test: a wait on an mbarrier that nothing completes.  The bounded
+// wait gives up after limit_ns, the kernel records LP_ETIMEOUT in the error word and
+// returns; no fault, no trap, and the context stays usable.
+// ---------------------------------------------------------------------------------
+__global__ void wait_probe_kernel(int *err, uint64_t limit_ns)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, &abort, limit_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+// Algorithm 1 (Preprocess): the cloud turns the client's zero-phase samples into
+// encryptions of its service bits by adding the encoding (0, f(bit)) to each.
+__global__ void preprocess_kernel(int n, const uint32_t *zero, const uint8_t *bits, uint32_t *out, size_t count)
+{
+    const size_t total = count * (size_t)(n + 1);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t g = idx / (n + 1);
+        const int w = (int)(idx % (n + 1));
+        uint32_t v = zero[idx];
+        if (w == n) v += bits[g] ? T_EIGHTH : 0u - T_EIGHTH;
+        out[idx] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------------
 static int grid_for(size_t work, int threads, int num_sms)
@@ -297,6 +330,20 @@ cudaError_t launch_keygen_ksk(int n, const uint8_t *s, const uint8_t *S, const u
 {
     const size_t total = (size_t)RING_N * KS_T * KS_BASE;
     keygen_ksk_kernel<<<grid_for(total * 32, 256, num_sms), 256, 0, st>>>(n, s, S, mask, noise, ksk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(int *err, uint64_t limit_ns, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(err, limit_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(int n, const uint32_t *zero, const uint8_t *bits, uint32_t *out, size_t count,
+                              int num_sms, cudaStream_t st)
+{
+    if (!count) return cudaSuccess;
+    preprocess_kernel<<<grid_for(count * (n + 1), 256, num_sms), 256, 0, st>>>(n, zero, bits, out, count);
     return cudaGetLastError();
 }
 

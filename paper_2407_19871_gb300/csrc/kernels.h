@@ -51,6 +51,10 @@ cudaError_t launch_keygen_bsk(int n, const uint8_t *s, const uint8_t *S, const u
 cudaError_t launch_keygen_ksk(int n, const uint8_t *s, const uint8_t *S, const uint32_t *mask,
                               const uint32_t *noise, uint32_t *ksk, int num_sms, cudaStream_t st);
 
+cudaError_t launch_wait_probe(int *err, uint64_t limit_ns, cudaStream_t st);
+cudaError_t launch_preprocess(int n, const uint32_t *zero, const uint8_t *bits, uint32_t *out, size_t count,
+                              int num_sms, cudaStream_t st);
+
 // Twiddle and constant tables (host side) uploaded at context creation.
 struct NttTables {
     uint32_t prime[2];                  // the two NTT primes

@@ -207,6 +207,7 @@ extern "C" int lp_create(const lp_params *p, int device, lp_ctx **out)
 extern "C" int lp_destroy(lp_ctx *c)
 {
     if (!c) return LP_OK;
+    if (c->server) lp_server_stop(c);
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto &t : c->timers) {
@@ -595,4 +596,25 @@ extern "C" int lp_client_keygen_ksk(const lp_params *p, const uint8_t *s, const 
     if (!s || !S || !mask || !noise || !ksk) return fail(LP_EINVAL, "null pointer");
     cudaError_t e = launch_keygen_ksk(p->n, s, S, mask, noise, ksk, device_sms(), static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? LP_OK : cuda_fail(e, "keygen_ksk launch");
+}
+
+extern "C" int lp_preprocess_services(int n, const uint32_t *zero, const uint8_t *bits, uint32_t *out, size_t count,
+                                      void *stream)
+{
+    if (n < 1 || n > MAX_LWE_N) return fail(LP_EINVAL, "bad n=%d", n);
+    if (count == 0) return LP_OK;
+    if (!zero || !bits || !out) return fail(LP_EINVAL, "null pointer");
+    cudaError_t e = launch_preprocess(n, zero, bits, out, count, device_sms(), static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "preprocess launch");
+}
+
+extern "C" int lp_selftest_wait_timeout(lp_ctx *c, uint32_t limit_ms, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (limit_ms == 0 || limit_ms > 10000) return fail(LP_EINVAL, "limit_ms=%u outside [1, 10000]", limit_ms);
+    cudaSetDevice(c->device);
+    cudaError_t e = launch_wait_probe(static_cast<int *>(c->err.ptr), (uint64_t)limit_ms * 1000000ull,
+                                      static_cast<cudaStream_t>(stream));
+    c->launches++;
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "wait probe launch");
 }

@@ -15,6 +15,8 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+struct Server;
+
 struct KernelTimer {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     double ms = 0.0;
@@ -37,6 +39,7 @@ struct lp_ctx {
     bool timing = false;
     uint64_t launches = 0;
     std::map<std::string, lp::KernelTimer> timers;
+    lp::Server *server = nullptr;   // query server (lp_server_start), if running
 };
 
 namespace lp {

@@ -29,7 +29,12 @@ EXPORTS = [
     "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch",
     "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
     "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
+    "lp_preprocess_services", "lp_selftest_wait_timeout",
+    "lp_server_start", "lp_server_submit", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
+    "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
+    "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy",
 ]
+LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
 
 
 class lp_params(ctypes.Structure):
@@ -40,6 +45,13 @@ class lp_query(ctypes.Structure):
     _fields_ = [("l", ctypes.c_int), ("is_signed", ctypes.c_int), ("n_boxes", ctypes.c_int), ("m", ctypes.c_int),
                 ("comb", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("boxes", ctypes.c_void_p),
                 ("services", ctypes.c_void_p), ("out_service", ctypes.c_void_p)]
+
+
+class lp_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "rejected", "waiting", "active",
+                                               "ticks", "bootstraps")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "elapsed_s", "queries_per_s",
+                                               "bootstraps_per_s")]
 
 
 class LocpirError(RuntimeError):
@@ -88,6 +100,23 @@ def lib() -> ctypes.CDLL:
             "lp_kernel_time": (i, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_uint64)]),
             "lp_reset_timing": (i, [vp]),
+            "lp_preprocess_services": (i, [i, vp, vp, vp, sz, vp]),
+            "lp_selftest_wait_timeout": (i, [vp, u32, vp]),
+            "lp_server_start": (i, [vp, sz, i]),
+            "lp_server_submit": (i, [vp, ctypes.POINTER(lp_query), ctypes.POINTER(ctypes.c_uint64)]),
+            "lp_server_poll": (i, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+            "lp_server_wait": (i, [vp, ctypes.c_uint64, u32]),
+            "lp_server_stats": (i, [vp, ctypes.POINTER(lp_stats)]),
+            "lp_server_stop": (i, [vp]),
+            "lp_save_keys_file": (i, [P, vp, vp, ctypes.c_char_p]),
+            "lp_verify_keys_file": (i, [ctypes.c_char_p, P]),
+            "lp_load_keys_file": (i, [vp, ctypes.c_char_p]),
+            "lp_sha256": (i, [vp, sz, ctypes.c_char_p]),
+            "lp_plan_locpir": (i, [vp, ctypes.POINTER(lp_query), sz, ctypes.POINTER(vp)]),
+            "lp_plan_run": (i, [vp, vp]),
+            "lp_plan_info": (i, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)]),
+            "lp_plan_destroy": (i, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -154,6 +183,54 @@ def lp_client_keygen_ksk(params, s, S, mask, noise, ksk, stream=None):
                                       _dptr(ksk), _stream(stream)), "lp_client_keygen_ksk")
 
 
+def lp_sha256(data: bytes) -> bytes:
+    out = ctypes.create_string_buffer(32)
+    _check(lib().lp_sha256(data, len(data), out), "lp_sha256")
+    return out.raw
+
+
+def lp_save_keys_file(params: lp_params, bsk: np.ndarray, ksk: np.ndarray, path: str) -> None:
+    _check(lib().lp_save_keys_file(ctypes.byref(params), _hptr(bsk), _hptr(ksk), path.encode()), "lp_save_keys_file")
+
+
+def lp_verify_keys_file(path: str) -> lp_params:
+    p = lp_params()
+    _check(lib().lp_verify_keys_file(path.encode(), ctypes.byref(p)), "lp_verify_keys_file")
+    return p
+
+
+def lp_preprocess_services(n, zero, bits, out, count, stream=None):
+    _check(lib().lp_preprocess_services(n, _dptr(zero), _dptr(bits), _dptr(out), count, _stream(stream)),
+           "lp_preprocess_services")
+
+
+class Plan:
+    """An lp_plan (a LocPIR batch captured in a CUDA graph); keeps its query tensors alive."""
+
+    def __init__(self, h, queries):
+        self.h = h
+        self.queries = queries
+
+    def lp_plan_run(self, stream=None) -> None:
+        _check(lib().lp_plan_run(self.h, _stream(stream)), "lp_plan_run")
+
+    def lp_plan_info(self) -> dict:
+        a, b, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().lp_plan_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)), "lp_plan_info")
+        return {"blind_rotations": a.value, "key_switches": b.value, "kernels": k.value}
+
+    def lp_plan_destroy(self) -> None:
+        if self.h:
+            lib().lp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.lp_plan_destroy()
+        except Exception:
+            pass
+
+
 class Context:
     """An lp_ctx: keys and scratch on one device.  Methods mirror the lp_* entry points."""
 
@@ -192,6 +269,9 @@ class Context:
 
     def lp_load_bsk_device(self, bsk, stream=None) -> None:
         _check(lib().lp_load_bsk_device(self.h, _dptr(bsk), bsk.numel(), _stream(stream)), "lp_load_bsk_device")
+
+    def lp_load_keys_file(self, path: str) -> None:
+        _check(lib().lp_load_keys_file(self.h, path.encode()), "lp_load_keys_file")
 
     def lp_load_ksk_device(self, ksk, stream=None) -> None:
         _check(lib().lp_load_ksk_device(self.h, _dptr(ksk), ksk.numel(), _stream(stream)), "lp_load_ksk_device")
@@ -239,18 +319,63 @@ class Context:
                                      _dptr(services, n_boxes * m * W, "services"), comb,
                                      _dptr(out_service, m * W, "out_service"), _stream(stream)), "lp_locpir_query")
 
+    def _query_struct(self, q: dict) -> lp_query:
+        W = self.n + 1
+        l, nb, m = q["l"], q["n_boxes"], q["m"]
+        return lp_query(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
+                        _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"),
+                        _dptr(q["boxes"], nb * 4 * l * W, "boxes"), _dptr(q["services"], nb * m * W, "services"),
+                        _dptr(q["out_service"], m * W, "out_service"))
+
     def lp_locpir_batch(self, queries: list[dict], stream=None) -> None:
         """queries: dicts with l, is_signed, n_boxes, m, comb and tensors x, y, boxes,
         services, out_service (shapes as in lp_locpir_query)."""
-        W = self.n + 1
         arr = (lp_query * len(queries))()
         for i, q in enumerate(queries):
-            l, nb, m = q["l"], q["n_boxes"], q["m"]
-            arr[i] = lp_query(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
-                              _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"),
-                              _dptr(q["boxes"], nb * 4 * l * W, "boxes"), _dptr(q["services"], nb * m * W, "services"),
-                              _dptr(q["out_service"], m * W, "out_service"))
+            arr[i] = self._query_struct(q)
         _check(lib().lp_locpir_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_batch")
+
+    # ---- plans (CUDA graphs)
+    def lp_plan_locpir(self, queries: list[dict]) -> "Plan":
+        arr = (lp_query * len(queries))()
+        for i, q in enumerate(queries):
+            arr[i] = self._query_struct(q)
+        h = ctypes.c_void_p()
+        _check(lib().lp_plan_locpir(self.h, arr, len(queries), ctypes.byref(h)), "lp_plan_locpir")
+        return Plan(h, queries)
+
+    # ---- server (continuous batching)
+    def lp_server_start(self, mem_budget: int, policy: int = LP_SERVER_QUEUE) -> None:
+        self._server_refs = {}
+        _check(lib().lp_server_start(self.h, mem_budget, policy), "lp_server_start")
+
+    def lp_server_submit(self, q: dict) -> int:
+        """Submit a query dict (as in lp_locpir_batch); its tensors are kept referenced here
+        until lp_server_stop, since the server reads them asynchronously."""
+        t = ctypes.c_uint64()
+        qs = self._query_struct(q)
+        _check(lib().lp_server_submit(self.h, ctypes.byref(qs), ctypes.byref(t)), "lp_server_submit")
+        self._server_refs[t.value] = q
+        return t.value
+
+    def lp_server_poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().lp_server_poll(self.h, ticket, ctypes.byref(d)), "lp_server_poll")
+        return bool(d.value)
+
+    def lp_server_wait(self, ticket: int, timeout_ms: int = 600000) -> None:
+        _check(lib().lp_server_wait(self.h, ticket, timeout_ms), "lp_server_wait")
+
+    def lp_server_stats(self) -> dict:
+        st = lp_stats()
+        _check(lib().lp_server_stats(self.h, ctypes.byref(st)), "lp_server_stats")
+        return {k: getattr(st, k) for k, _ in lp_stats._fields_}
+
+    def lp_server_stop(self) -> None:
+        try:
+            _check(lib().lp_server_stop(self.h), "lp_server_stop")
+        finally:
+            self._server_refs = {}
 
     # ---- runtime
     def lp_sync(self) -> None:
@@ -269,3 +394,6 @@ class Context:
 
     def lp_reset_timing(self) -> None:
         _check(lib().lp_reset_timing(self.h), "lp_reset_timing")
+
+    def lp_selftest_wait_timeout(self, limit_ms: int, stream=None) -> None:
+        _check(lib().lp_selftest_wait_timeout(self.h, limit_ms, _stream(stream)), "lp_selftest_wait_timeout")

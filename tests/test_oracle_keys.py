@@ -105,3 +105,19 @@ def test_ciphertext_sizes_match_paper():
             got = kib(n, int(l))
             assert math.floor(got * 10) / 10 == kb or math.floor(got) == kb
     assert synth.DEFAULT.n == n128
+
+
+def test_preprocess_alg1_phase_and_decryption(keys):
+    """Algorithm 1: the zero-phase sample plus (0, f(bit)) has phase f(bit) + e exactly and
+    decrypts to the bit."""
+    n, cnt = keys.params.n, 40
+    bits = synth.bits(81, 1, cnt)
+    dr = synth.lwe_draws(81, cnt)
+    zero = oracle.zero_samples(keys.s, dr)
+    ph0 = oracle.phase(keys.s, zero)
+    np.testing.assert_array_equal(ph0, dr.noise)  # phase 0 + e
+    ct = oracle.preprocess(zero, bits)
+    want = (oracle.encode(bits).astype(np.uint64) + dr.noise.astype(np.uint64)) % M32
+    np.testing.assert_array_equal(oracle.phase(keys.s, ct), want)
+    np.testing.assert_array_equal(oracle.decrypt(keys.s, ct), bits)
+    np.testing.assert_array_equal(ct[:, :n], zero[:, :n])
