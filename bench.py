@@ -38,6 +38,10 @@ MODMUL_PER_STEP = 2 * ((6 + 2) * 5120 + 12 * 1024)
 # multiply-adds per SM per clock / 3 multiply-adds per Shoup modular multiplication.
 SMS, MAX_MHZ, IMAD_PER_CLK_SM, IMAD_PER_MODMUL = 152, 2070.0, 64, 3
 PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * IMAD_PER_CLK_SM / IMAD_PER_MODMUL
+# The same peak with the measured cost of one lazy Shoup product on GB300 (16.0 per SM per
+# clock: its multiply-high runs at half rate), from paper_2407_19871_gb300/peaks/int_peaks.cu.
+MEASURED_SHOUP_PER_CLK_SM = 16.0
+MEASURED_PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * MEASURED_SHOUP_PER_CLK_SM
 
 
 def _dist():
@@ -104,6 +108,28 @@ def _dev(a):
     return torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
 
 
+def reduce_max(x: float, dist) -> float:
+    """Maximum of x over all ranks (a time: the job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, steps: int, max_seconds: float) -> float:
+    """Whole-job units per second: every rank processes its own batch (weak scaling)."""
+    return units_per_rank * world * steps / max_seconds
+
+
+def rank_seed(rank: int) -> int:
+    """Input seed of a rank's batch: seed 1 on rank 0 (the workload's own seed), distinct
+    seeds on the others, so that ranks never duplicate work."""
+    return 1 if rank == 0 else 1000 + rank
+
+
 def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int = COUNT):
     """Keys generated on the device from the seed-0 draws, inputs encrypted on the device."""
     import torch
@@ -131,6 +157,59 @@ def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int =
         cts.append(out)
     torch.cuda.synchronize()
     return ctx, p, s_dev, (A, B), cts
+
+
+def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2) -> dict:
+    """LocPIR queries/s on the city-batch shape (l = 32 unsigned, one box, 256-bit service,
+    half of the points inside): nq queries scheduled together and captured in a CUDA graph
+    (lp_plan_locpir); one warm-up replay, one timed replay (CUDA events).  Every output is
+    decrypted on the device and compared with the plaintext truth."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    l, m = 32, 256
+    qs = synth.city_batch(seed, nq, l, m)
+    per_q = 2 * l + 4 * l + m
+    bits = np.zeros(nq * per_q, np.uint8)
+    for k, q in enumerate(qs):
+        row = [synth.int_to_bits(q.x, l), synth.int_to_bits(q.y, l)] + \
+              [synth.int_to_bits(v, l) for v in q.box] + [q.service]
+        bits[k * per_q:(k + 1) * per_q] = np.concatenate(row)
+    dr = synth.lwe_draws(seed, len(bits))
+    mu = np.where(bits == 1, 1 << 29, (1 << 32) - (1 << 29)).astype(np.uint32)
+    W = p.n + 1
+    ct = torch.empty(len(bits), W, dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_encrypt(p.n, s_dev, _dev(dr.mask), _dev(dr.noise), _dev(mu), ct, len(bits))
+    out = torch.empty(nq * m, W, dtype=torch.int32, device="cuda")
+    queries = []
+    for k in range(nq):
+        b = k * per_q
+        queries.append(dict(l=l, is_signed=0, n_boxes=1, m=m, comb=locpir.LP_XOR_TREE, x=ct[b:b + l],
+                            y=ct[b + l:b + 2 * l], boxes=ct[b + 2 * l:b + 6 * l], services=ct[b + 6 * l:b + per_q],
+                            out_service=out[k * m:(k + 1) * m]))
+    plan = ctx.lp_plan_locpir(queries)
+    info = plan.lp_plan_info()
+    st = torch.cuda.current_stream()
+    plan.lp_plan_run(st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    plan.lp_plan_run(st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    ph = torch.empty(nq * m, dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, nq * m)
+    got = (ph.cpu().numpy() > 0).astype(np.uint8).reshape(nq, m)
+    wrong = 0
+    for k, q in enumerate(qs):
+        x1, x2, y1, y2 = q.box
+        inside = x1 <= q.x < x2 and y1 <= q.y < y2
+        wrong += int((got[k] != (q.service if inside else 0)).sum())
+    plan.lp_plan_destroy()
+    return {"queries_per_s": nq / sec, "queries": nq, "seconds": sec,
+            "blind_rotations_per_s": info["blind_rotations"] / sec, "blind_rotations": info["blind_rotations"],
+            "kernels_per_run": info["kernels"], "wrong_bits": wrong,
+            "shape": "city batch: l=32 unsigned, 1 box, m=256, half the points inside (seed 2), CUDA-graph plan"}
 
 
 def check_outputs(p, s_dev, out, A, B) -> int:
@@ -202,7 +281,7 @@ def run_gpu(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(local, count=COUNT)
+    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(local, seed_inputs=rank_seed(rank), count=COUNT)
     out = torch.empty_like(a)
     st = torch.cuda.current_stream()
 
@@ -237,11 +316,8 @@ def run_gpu(args) -> None:
     br_ms, br_n = ctx.lp_kernel_time("br")
     ks_ms, ks_n = ctx.lp_kernel_time("ks")
     ctx.lp_set_timing(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = COUNT * world * args.steps / (ms / 1e3)
+    ms = reduce_max(ms, dist)
+    value = job_throughput(COUNT, world, args.steps, ms / 1e3)
 
     # ---- end to end through the host-pointer entry point (pinned host buffers)
     W = p.n + 1
@@ -259,11 +335,8 @@ def run_gpu(args) -> None:
     for _ in range(e2e_steps):
         ctx.lp_gate_batch_host(locpir.LP_NAND, na, nb, None, no, COUNT)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = COUNT * world * e2e_steps / e2e_s
+    e2e_s = reduce_max(e2e_s, dist)
+    e2e_value = job_throughput(COUNT, world, e2e_steps, e2e_s)
 
     # ---- per-gate path (same kernels, one gate per launch), on a sample
     per_gate = None
@@ -275,6 +348,10 @@ def run_gpu(args) -> None:
             ctx.lp_gate_batch(locpir.LP_NAND, a[g:g + 1], b[g:g + 1], None, out[g:g + 1], 1, st)
             torch.cuda.synchronize()
         per_gate = k / (time.perf_counter() - g0)
+
+    loc = None
+    if rank == 0 and args.locpir_queries > 0:
+        loc = locpir_throughput(ctx, p, s_dev, args.locpir_queries)
 
     if rank != 0:
         if dist:
@@ -302,11 +379,14 @@ def run_gpu(args) -> None:
         "roofline": {"bound": "alu", "kernel": "br_kernel (blind rotation + extraction)",
                      "achieved": achieved / 1e12, "peak": PEAK_MODMUL_PER_S / 1e12, "unit": "Tmodmul/s",
                      "frac": achieved / PEAK_MODMUL_PER_S, "traffic": traffic,
+                     "peak_measured_shoup": MEASURED_PEAK_MODMUL_PER_S / 1e12,
+                     "frac_of_measured_shoup": achieved / MEASURED_PEAK_MODMUL_PER_S,
                      "br_ms_per_launch": br_avg_ms, "ks_ms_per_launch": ks_ms / max(ks_n, 1)},
         "clocks": clk,
         "per_gate_bootstraps_per_s": per_gate,
         "batched_speedup_vs_per_gate": (value / world / per_gate) if per_gate else None,
         "decrypt_errors": wrong,
+        "locpir": loc,
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -324,6 +404,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--per-gate", type=int, default=16, help="gates timed one per launch (0: skip)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--locpir-queries", type=int, default=152,
+                    help="LocPIR queries of the city-batch shape timed for queries/s (0: skip)")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="gates per step (default 65,536; smaller values are for profiling only)")
     args = ap.parse_args()
