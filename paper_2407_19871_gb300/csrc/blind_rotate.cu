@@ -24,7 +24,8 @@
 // each warp forward-transforms the 6 digit polynomials modulo its prime and multiplies
 // them with the key chunk, accumulating both output components in 64-bit registers
 // (key stored as NTT(b) N^-1 2^32 mod p, one Montgomery reduction per coefficient);
-// it inverse-transforms the 2 sums.  The pair then swaps half of its residues through
+// it inverse-transforms the 2 sums together (their butterflies interleaved).  The pair then
+// swaps half of its residues through
 // shared memory: the prime-0 warp recombines component 0 (centred CRT) and adds it to
 // ACC, the prime-1 warp component 1.
 #include "common.cuh"
@@ -112,6 +113,46 @@ __device__ __forceinline__ bool drain(BrSmem &sm, const Producer &pr)
     return ok;
 }
 
+// Wait for the next key chunk of this prime, multiply-accumulate the transformed digit x into
+// both output components (64-bit sums), release the chunk, and (producer lane) refill the ring.
+__device__ __forceinline__ void mac_chunk(BrSmem &sm, int pi, int lane, bool work, bool &ok, uint32_t &cseq,
+                                          const uint32_t (&x)[32], unsigned long long (&acc0)[32],
+                                          unsigned long long (&acc1)[32], Producer &pr, bool producer)
+{
+    const uint32_t rs = cseq % BR_RING;
+    const uint32_t par = (cseq / BR_RING) & 1u;
+    if (ok && !mbar_wait_bounded(&sm.full_bar[pi][rs], par, &sm.abort)) {
+        ok = false;
+        if (lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+    }
+    if (work && ok) {
+        // x in [0, 2p), key in [0, p): six products sum below 12 p^2 < 2^32 p.
+        const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs]);
+        const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs] + RING_N);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint4 b0 = ch0[q * 32 + lane];
+            const uint4 b1 = ch1[q * 32 + lane];
+            const uint32_t bb0[4] = {b0.x, b0.y, b0.z, b0.w};
+            const uint32_t bb1[4] = {b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int k = 4 * q + e;
+                acc0[k] += (unsigned long long)x[k] * bb0[e];
+                acc1[k] += (unsigned long long)x[k] * bb1[e];
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        mbar_arrive(&sm.empty_bar[pi][rs]);
+        // Refill the slot released one chunk ago (BR_RING - 1 chunks of lookahead).
+        if (producer) produce(sm, pr, cseq + BR_RING);
+    }
+    __syncwarp();
+    cseq++;
+}
+
 // One external-product half for prime pi: rotate/decompose ACC, 6 forward NTTs each
 // followed by the 64-bit multiply-accumulate with the streamed key chunk, 2 inverse NTTs.
 // On return `mine` holds component pi of the product mod p (in [0, p), layout A) and
@@ -144,62 +185,32 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
                 U[j] = v - A[j] + GADGET_OFF;
             }
         }
+        // digit + 512 in [0, 1024), shifted by p - 512 into [p - 512, p + 512) = digit mod p.
 #pragma unroll 1
         for (int p = 0; p < LG; p++) {
             const int sh = 22 - BGBIT * p;
             if (work) {
-                // digit + 512 in [0, 1024), shifted by p - 512 into [p - 512, p + 512) = digit mod p.
 #pragma unroll
                 for (int k = 0; k < 32; k++) x[k] = ((U[lane + 32 * k] >> sh) & 1023u) + (K.p - 512u);
                 ntt_fwd(x, tbuf, twf, lane, pi, K);
             }
-            const uint32_t rs = cseq % BR_RING;
-            const uint32_t par = (cseq / BR_RING) & 1u;
-            if (ok && !mbar_wait_bounded(&sm.full_bar[pi][rs], par, &sm.abort)) {
-                ok = false;
-                if (lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
-            }
-            if (work && ok) {
-                // x in [0, 2p), key in [0, p): six products sum below 12 p^2 < 2^32 p.
-                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs]);
-                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs] + RING_N);
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const uint4 b0 = ch0[q * 32 + lane];
-                    const uint4 b1 = ch1[q * 32 + lane];
-                    const uint32_t bb0[4] = {b0.x, b0.y, b0.z, b0.w};
-                    const uint32_t bb1[4] = {b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int k = 4 * q + e;
-                        acc0[k] += (unsigned long long)x[k] * bb0[e];
-                        acc1[k] += (unsigned long long)x[k] * bb1[e];
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&sm.empty_bar[pi][rs]);
-                // Refill the slot released one chunk ago (BR_RING - 1 chunks of lookahead).
-                if (producer) produce(sm, pr, cseq + BR_RING);
-            }
-            __syncwarp();
-            cseq++;
+            mac_chunk(sm, pi, lane, work, ok, cseq, x, acc0, acc1, pr, producer);
         }
     }
     if (work && ok) {
-#pragma unroll 1
-        for (int c = 0; c < 2; c++) {
+        // Both output components inverse-transformed together (independent butterflies interleave).
+        uint32_t y[2][32];
 #pragma unroll
-            for (int k = 0; k < 32; k++) x[k] = redc64(c == 0 ? acc0[k] : acc1[k], K);
-            ntt_inv(x, tbuf, twi, lane, pi, K);
-            if (c == pi) {
+        for (int k = 0; k < 32; k++) {
+            y[0][k] = redc64(acc0[k], K);
+            y[1][k] = redc64(acc1[k], K);
+        }
+        ntt_inv_multi<2>(y, tbuf, twi, lane, pi, K);
 #pragma unroll
-                for (int k = 0; k < 32; k++) mine[k] = umin_u32(x[k], x[k] - K.p);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 32; k++) sm.xch[slot][c][lane + 32 * k] = umin_u32(x[k], x[k] - K.p);
-            }
+        for (int k = 0; k < 32; k++) {
+            const uint32_t r0 = umin_u32(y[0][k], y[0][k] - K.p), r1 = umin_u32(y[1][k], y[1][k] - K.p);
+            mine[k] = pi == 0 ? r0 : r1;
+            sm.xch[slot][1 - pi][lane + 32 * k] = pi == 0 ? r1 : r0;
         }
     }
     return ok;

@@ -108,9 +108,11 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const
     for (int k = 0; k < 32; k++) x[k] -= __umulhi(x[k], K.rp) * K.p;
 }
 
-// Input in [0, 2p) (layout B), output in [0, 2p) (layout A).
-__device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane, int pi,
-                                        const PrimeK &K)
+// Inverse transform of NP polynomials together (butterflies of the same position interleaved,
+// for instruction-level parallelism).  Input in [0, 2p) (layout B), output in [0, 2p) (layout A).
+template <int NP>
+__device__ __forceinline__ void ntt_inv_multi(uint32_t (&x)[NP][32], uint32_t *tbuf, const uint2 *tw, int lane,
+                                              int pi, const PrimeK &K)
 {
 #pragma unroll
     for (int s = 9; s >= 5; s--) {
@@ -122,16 +124,20 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const
 #pragma unroll
             for (int o = 0; o < L; o++) {
                 const int k = b * 2 * L + o;
-                bfly_inv(x[k], x[k + L], z.x, z.y, K);
+#pragma unroll
+                for (int q = 0; q < NP; q++) bfly_inv(x[q][k], x[q][k + L], z.x, z.y, K);
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 32; k++) tbuf[lane * 33 + k] = x[k];
-    __syncwarp();
+    for (int q = 0; q < NP; q++) {
 #pragma unroll
-    for (int k = 0; k < 32; k++) x[k] = tbuf[k * 33 + lane];
-    __syncwarp();
+        for (int k = 0; k < 32; k++) tbuf[lane * 33 + k] = x[q][k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 32; k++) x[q][k] = tbuf[k * 33 + lane];
+        __syncwarp();
+    }
 #pragma unroll
     for (int s = 4; s >= 0; s--) {
         const int D = 16 >> s;
@@ -139,7 +145,8 @@ __device__ __forceinline__ void ntt_inv(uint32_t (&x)[32], uint32_t *tbuf, const
         for (int k = 0; k < 32; k++) {
             if (k & D) continue;
             const uint2 z = c_tw[pi][1][(1 << s) + (k >> (5 - s))];
-            bfly_inv(x[k], x[k + D], z.x, z.y, K);
+#pragma unroll
+            for (int q = 0; q < NP; q++) bfly_inv(x[q][k], x[q][k + D], z.x, z.y, K);
         }
     }
 }
