@@ -244,6 +244,21 @@ def cpu_baseline(seconds_target: float = 15.0) -> dict:
             "sample": f"first {S} of the 65,536 NAND gates (OpenMP over gates, {cores} threads), {dt:.1f} s"}
 
 
+def br_traffic():
+    """DRAM bytes per blind-rotation launch from the recorded ncu capture, or None once the
+    kernel sources differ from the ones the counters were taken on."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["source_files"]))
+        if h.hexdigest() != rec["br_kernel_source_sha256"]:
+            return None
+        return rec["br_kernel_dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def run_reference(args) -> None:
     rank, world, _ = _dist()
     if rank != 0:
@@ -359,12 +374,7 @@ def run_gpu(args) -> None:
         return
     br_avg_ms = br_ms / max(br_n, 1)
     achieved = COUNT * N_LWE * MODMUL_PER_STEP / (br_avg_ms / 1e3)
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("br_kernel_dram_bytes_per_launch")
-    except Exception:
-        traffic = None
+    traffic = br_traffic()
     line = {
         "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
