@@ -126,7 +126,7 @@ __device__ __forceinline__ void mac_chunk(BrSmem &sm, int pi, int lane, bool wor
         if (lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
     }
     if (work && ok) {
-        // x in [0, 2p), key in [0, p): six products sum below 12 p^2 < 2^32 p.
+        // x in [0, 22p), key in [0, p): six products sum below 132 p^2 < 2^64.
         const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs]);
         const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.ring[pi][rs] + RING_N);
 #pragma unroll
@@ -192,18 +192,24 @@ __device__ __forceinline__ bool external_product(BrSmem &sm, int slot, int lane,
             if (work) {
 #pragma unroll
                 for (int k = 0; k < 32; k++) x[k] = ((U[lane + 32 * k] >> sh) & 1023u) + (K.p - 512u);
-                ntt_fwd(x, tbuf, twf, lane, pi, K);
+                ntt_fwd<false>(x, tbuf, twf, lane, pi, K);
             }
             mac_chunk(sm, pi, lane, work, ok, cseq, x, acc0, acc1, pr, producer);
         }
     }
     if (work && ok) {
-        // Both output components inverse-transformed together (independent butterflies interleave).
+        // Montgomery reduction of sums below 132 p^2 leaves [0, 132 p^2 / 2^32 + p) within [0, 7p)
+        // (p < 2^32 / 22); two conditional subtractions (ALU pipe, not the multiplier) bring
+        // it into [0, 2p).  Both components are then inverse-transformed together.
         uint32_t y[2][32];
 #pragma unroll
         for (int k = 0; k < 32; k++) {
-            y[0][k] = redc64(acc0[k], K);
-            y[1][k] = redc64(acc1[k], K);
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint32_t v = redc64(q == 0 ? acc0[k] : acc1[k], K);
+                v = umin_u32(v, v - 2u * K.p2);
+                y[q][k] = umin_u32(v, v - K.p2);
+            }
         }
         ntt_inv_multi<2>(y, tbuf, twi, lane, pi, K);
 #pragma unroll
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, ui
             if (m < 0) m += K.p;
             x[k] = (uint32_t)m;
         }
-        ntt_fwd(x, sm.tbuf[warp], sm.tw[pi], lane, pi, K);
+        ntt_fwd<true>(x, sm.tbuf[warp], sm.tw[pi], lane, pi, K);
         const uint64_t sc = pi == 0 ? scale0 : scale1;   // N^-1 2^32 mod p
         uint32_t *dst = bsk_hat + ((i * 2 + pi) * ROWS + r) * CHUNK_WORDS + c * RING_N;
 #pragma unroll

@@ -69,8 +69,9 @@ __device__ __forceinline__ void bfly_inv(uint32_t &x, uint32_t &y, uint32_t w, u
 
 // tbuf: this warp's 32 x 33 word transpose buffer; tw: the lane table of this prime and
 // direction ([LANE_TW][32] (w, w')); slot base + b of stage s is block b of the lane's
-// 16 / L blocks (base = 2^(s-5) - 1).  Input in [0, 2p) (layout A), output in [0, 2p)
-// (layout B).
+// 16 / L blocks (base = 2^(s-5) - 1).  Input in [0, 2p) (layout A); output (layout B) in
+// [0, 2p) with Reduce, else in [0, 22p) (the caller reduces later, more cheaply).
+template <bool Reduce>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const uint2 *tw, int lane, int pi,
                                         const PrimeK &K)
 {
@@ -104,8 +105,10 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], uint32_t *tbuf, const
             }
         }
     }
+    if (Reduce) {
 #pragma unroll
-    for (int k = 0; k < 32; k++) x[k] -= __umulhi(x[k], K.rp) * K.p;
+        for (int k = 0; k < 32; k++) x[k] -= __umulhi(x[k], K.rp) * K.p;
+    }
 }
 
 // Inverse transform of NP polynomials together (butterflies of the same position interleaved,
@@ -151,7 +154,8 @@ __device__ __forceinline__ void ntt_inv_multi(uint32_t (&x)[NP][32], uint32_t *t
     }
 }
 
-// Montgomery reduction of T < 2^32 p: T 2^-32 mod p in [0, 2p).
+// Montgomery reduction: T 2^-32 mod p, as the exact value (T + m p) / 2^32 < T / 2^32 + p
+// (m = -T p^-1 mod 2^32); in [0, 2p) for T < 2^32 p.  The caller keeps it below 2^32.
 __device__ __forceinline__ uint32_t redc64(unsigned long long T, const PrimeK &K)
 {
     const uint32_t lo = (uint32_t)T, hi = (uint32_t)(T >> 32);
