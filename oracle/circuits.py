@@ -10,11 +10,13 @@ topological order.
 Followed passages (LocPIR, arXiv 2407.19871):
   * HomCompS: Algorithm 2 (Section 4.2) -- t0 = Enc(0); flip both MSBs; for each bit
     from index 0 (least significant) up: t1 = XNOR(c1[i], c2[i]); t0 = MUX(t1, t0, c2[i]).
-  * HomCompLE: "negating HomCompS" (Section 4.2), read as NOT(HomCompS(b, a)), i.e. a <= b.
+  * HomCompLE: the negation of HomCompS (Section 4.2), read as NOT(HomCompS(b, a)), i.e. a <= b.
   * LocPIR: Algorithm 3 (Section 4.3) -- four comparisons per box, three HomANDs,
     bitwiseAND (Algorithm 5) of the validation bit with the box's service, then the sum.
   * HomAddXOR: Algorithm 4 (Section 4.4); its body's assignment to S_i[j] is read as
     S[j].  The default combine is a pairwise XOR tree over boxes.
+Beyond the paper: comp_s_known / locpir_known, the same circuits when the server knows
+the box bounds in the clear (a comparator then costs at most l - 1 bootstraps, not 3l).
 Readings where the paper is silent or garbled are listed in the design notes.
 """
 from __future__ import annotations
@@ -84,6 +86,30 @@ def comp_le(net: Netlist, a: list[int], b: list[int], signed: bool) -> int:
     return net.NOT(comp_s(net, b, a, signed))
 
 
+def comp_s_known(net: Netlist, c1: list[int], K: int, signed: bool) -> int:
+    """HomCompS with a server-known second operand (beyond the paper): encrypts 1 iff
+    x1 < K.  Algorithm 2's steps with c2 replaced by the plaintext bits k_i of K:
+    XNOR(a, k) is a for k = 1 and NOT a for k = 0, and MUX(t1, t0, k) = t1 ? t0 : k is
+    AND(NOT a, t0) for k = 0 and OR(NOT a, t0) for k = 1.  While t0 is still a known
+    constant c, the step keeps c when k = c and yields NOT a otherwise, with no gate.
+    A constant result is returned as a trivial constant wire."""
+    l = len(c1)
+    cst, t0 = 0, None
+    for i in range(l):
+        a = c1[i]
+        k = (K >> i) & 1
+        if signed and i == l - 1:
+            a = net.NOT(a)
+            k ^= 1
+        na = net.NOT(a)
+        if t0 is None:
+            if k != cst:
+                t0 = na
+        else:
+            t0 = net.gate(OR if k else AND, na, t0)
+    return net.const(cst) if t0 is None else t0
+
+
 XOR_TREE, XOR_CHAIN, OR_TREE = 0, 1, 2
 
 
@@ -112,6 +138,30 @@ def locpir(net: Netlist, x: list[int], y: list[int], boxes: list[tuple[list[int]
         v2 = net.gate(AND, yl, yr)
         f = net.gate(AND, v1, v2)
         per_box.append([net.gate(AND, f, s) for s in svc])  # bitwiseAND, Algorithm 5
+    if comb == XOR_CHAIN:
+        m = len(services[0])
+        S = [net.const(0) for _ in range(m)]
+        for Si in per_box:
+            S = [net.gate(XOR, S[j], Si[j]) for j in range(m)]
+        return S
+    return _tree(net, OR if comb == OR_TREE else XOR, per_box)
+
+
+def locpir_known(net: Netlist, x: list[int], y: list[int], bounds: list[tuple[int, int, int, int]],
+                 services: list[list[int]], comb: int = XOR_TREE, signed: bool = False) -> list[int]:
+    """LocPIR with server-known box bounds (X1, X2, Y1, Y2) (beyond the paper): the four
+    comparisons of Algorithm 3 become X1 <= x = NOT(x < X1), x < X2, and the same for y,
+    each by comp_s_known; validation, bitwiseAND and the combine are Algorithm 3's."""
+    per_box = []
+    for (X1, X2, Y1, Y2), svc in zip(bounds, services):
+        xl = net.NOT(comp_s_known(net, x, X1, signed))
+        xr = comp_s_known(net, x, X2, signed)
+        yl = net.NOT(comp_s_known(net, y, Y1, signed))
+        yr = comp_s_known(net, y, Y2, signed)
+        v1 = net.gate(AND, xl, xr)
+        v2 = net.gate(AND, yl, yr)
+        f = net.gate(AND, v1, v2)
+        per_box.append([net.gate(AND, f, s) for s in svc])
     if comb == XOR_CHAIN:
         m = len(services[0])
         S = [net.const(0) for _ in range(m)]

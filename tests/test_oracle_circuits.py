@@ -166,3 +166,88 @@ def test_comparator_encrypted_l4(keys_noiseless):
     for (x1, x2), (_, _, lt, le) in zip(pairs, wires):
         assert oracle.decrypt(k.s, val[lt])[0] == int(x1 < x2)
         assert oracle.decrypt(k.s, val[le])[0] == int(x1 <= x2)
+
+
+# ---------------------------------------------------------------------------
+# Server-known bounds (beyond the paper).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("signed", [False, True])
+@pytest.mark.parametrize("l", [1, 2, 4])
+def test_comp_s_known_brute_force(signed, l):
+    """x < K for every encrypted x and known K of l bits, and the gate count: one
+    AND/OR per step after the first step whose bit differs from the running constant."""
+    for K in range(1 << l):
+        net = C.Netlist()
+        a = net.inputs(l)
+        lt = C.comp_s_known(net, a, K, signed)
+        kv = _signed(K, l) if signed else K
+        for x in range(1 << l):
+            vals = C.eval_plain(net, dict(zip(a, _bits(x, l))))
+            xv = _signed(x, l) if signed else x
+            assert vals[lt] == int(xv < kv), (x, K)
+        kb = _bits(K, l)
+        if signed:
+            kb[l - 1] ^= 1
+        first = next((i for i, b in enumerate(kb) if b != 0), None)
+        assert net.bootstraps()[0] == (0 if first is None else l - 1 - first)
+
+
+@pytest.mark.parametrize("comb", [C.XOR_TREE, C.XOR_CHAIN, C.OR_TREE])
+def test_locpir_known_matches_encrypted_bounds_l4(comb):
+    """The known-bounds circuit computes what Algorithm 3 computes with the same bounds
+    encrypted, for every point of a 4-bit grid."""
+    l, m = 4, 3
+    boxes = [(2, 9, 0, 16 - 1), (5, 6, 3, 12), (0, 1, 8, 9)]
+    services = [[1, 0, 1], [0, 1, 1], [1, 1, 0]]
+    net = C.Netlist()
+    x, y = net.inputs(l), net.inputs(l)
+    sw = [net.inputs(m) for _ in boxes]
+    out = C.locpir_known(net, x, y, boxes, sw, comb, False)
+    for px, py in itertools.product(range(16), repeat=2):
+        inputs = dict(zip(x, _bits(px, l)))
+        inputs.update(zip(y, _bits(py, l)))
+        for w, sv in zip(sw, services):
+            inputs.update(zip(w, sv))
+        vals = C.eval_plain(net, inputs)
+        want = [0] * m
+        for (x1, x2, y1, y2), sv in zip(boxes, services):
+            if x1 <= px < x2 and y1 <= py < y2:
+                want = [(u | v) if comb == C.OR_TREE else (u ^ v) for u, v in zip(want, sv)]
+        assert [vals[o] for o in out] == want, (px, py)
+
+
+def test_locpir_known_bootstrap_count():
+    """Per box the known-bounds circuit needs at most 4(l - 1) + 3 + m blind rotations,
+    against 12l + 3 + m with encrypted bounds."""
+    l, m = 16, 8
+    rng = np.random.default_rng(5)
+    bounds = [tuple(int(v) for v in rng.integers(0, 1 << l, 4)) for _ in range(5)]
+    net = C.Netlist()
+    x, y = net.inputs(l), net.inputs(l)
+    sw = [net.inputs(m) for _ in bounds]
+    C.locpir_known(net, x, y, bounds, sw, C.XOR_TREE, False)
+    br, ks = net.bootstraps()
+    assert br == ks
+    assert br <= 5 * (4 * (l - 1) + 3 + m) + 4 * m
+
+
+@pytest.mark.slow
+def test_comparator_known_encrypted_l4(keys_noiseless):
+    """Encrypted x against known K at l = 4 (signed and unsigned) decrypts to truth."""
+    k = keys_noiseless
+    l = 4
+    cases = [(3, 11, False), (11, 3, False), (7, 7, False), (12, 3, True), (3, 12, True)]
+    net = C.Netlist()
+    wires = []
+    for _ in cases:
+        wires.append(net.inputs(l))
+    outs = [C.comp_s_known(net, a, K, sg) for a, (_, K, sg) in zip(wires, cases)]
+    inputs = {}
+    for j, ((x, _, _), a) in enumerate(zip(cases, wires)):
+        ct = oracle.encrypt(k.s, _bits(x, l), synth.lwe_draws(71, l, offset=j * l))
+        inputs.update(zip(a, ct))
+    val = C.eval_encrypted(net, k, inputs)
+    for (x, K, sg), o in zip(cases, outs):
+        xv, kv = (_signed(x, l), _signed(K, l)) if sg else (x, K)
+        assert oracle.decrypt(k.s, val[o])[0] == int(xv < kv)
