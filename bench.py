@@ -212,6 +212,51 @@ def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2) -> dict:
             "shape": "city batch: l=32 unsigned, 1 box, m=256, half the points inside (seed 2), CUDA-graph plan"}
 
 
+def known_bounds_throughput(ctx, p, s_dev, nq: int, seed: int = 5) -> dict:
+    """City-shaped queries (l = 32 unsigned, one box, m = 256) evaluated twice through the
+    batch entry points: with the box bounds encrypted (lp_locpir_batch) and known to the
+    server (lp_locpir_known_batch).  Blind rotations counted from the circuits' gate counts
+    as the library schedules them (MUX = 2); outputs decrypted and checked."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    l, m = 32, 256
+    qs = synth.city_batch(seed, nq, l, m)
+    per_q = 2 * l + 4 * l + m
+    bits = np.concatenate([np.concatenate([synth.int_to_bits(q.x, l), synth.int_to_bits(q.y, l)] +
+                                          [synth.int_to_bits(v, l) for v in q.box] + [q.service]) for q in qs])
+    ct = _encrypt_bits(p, s_dev, bits, seed + 100)
+    W = p.n + 1
+    out_e = torch.empty(nq * m, W, dtype=torch.int32, device="cuda")
+    out_k = torch.empty(nq * m, W, dtype=torch.int32, device="cuda")
+    enc, known = [], []
+    for k, q in enumerate(qs):
+        b = k * per_q
+        common = dict(l=l, is_signed=0, n_boxes=1, m=m, comb=locpir.LP_XOR_TREE, x=ct[b:b + l], y=ct[b + l:b + 2 * l],
+                      services=ct[b + 6 * l:b + per_q])
+        enc.append(dict(common, boxes=ct[b + 2 * l:b + 6 * l], out_service=out_e[k * m:(k + 1) * m]))
+        known.append(dict(common, bounds=[q.box], out_service=out_k[k * m:(k + 1) * m]))
+    t_enc = _timed(lambda: ctx.lp_locpir_batch(enc), reps=1)
+    t_known = _timed(lambda: ctx.lp_locpir_known_batch(known), reps=1)
+    wrong = 0
+    for out in (out_e, out_k):
+        ph = torch.empty(nq * m, dtype=torch.int32, device="cuda")
+        locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, nq * m)
+        got = (ph.cpu().numpy() > 0).astype(np.uint8).reshape(nq, m)
+        for k, q in enumerate(qs):
+            x1, x2, y1, y2 = q.box
+            wrong += int((got[k] != (q.service if (x1 <= q.x < x2 and y1 <= q.y < y2) else 0)).sum())
+
+    def known_br(K: int) -> int:
+        # comp_s_known: one gate per bit after the first set bit (unsigned)
+        return 0 if K == 0 else l - 1 - (K & -K).bit_length() + 1
+
+    br_known = sum(sum(known_br(v) for v in q.box) + 3 + m for q in qs)
+    return {"experiment": "known_bounds", "queries": nq, "l": l, "m": m,
+            "encrypted_bounds_queries_per_s": nq / t_enc, "known_bounds_queries_per_s": nq / t_known,
+            "encrypted_bounds_blind_rotations": nq * (12 * l + 3 + m), "known_bounds_blind_rotations": br_known,
+            "wrong_bits": wrong}
+
+
 def check_outputs(p, s_dev, out, A, B) -> int:
     import torch
     from paper_2407_19871_gb300 import locpir
@@ -257,6 +302,219 @@ def br_traffic():
         return rec["br_kernel_dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+# ---------------------------------------------------------------------------------------
+# Paper experiment shapes on the GPU (Table 2, Fig. 4(a), Fig. 5's parallel width).
+# ---------------------------------------------------------------------------------------
+def _fixed(deg: float, frac: int) -> int:
+    """Section 4.1's fixed-point encoding: 9 integer bits, `frac` fraction bits, rounded half
+    away from zero (two's complement in l = 9 + frac bits)."""
+    v = deg * (1 << frac)
+    return int(np.floor(abs(v) + 0.5)) * (1 if v >= 0 else -1)
+
+
+def _encrypt_bits(p, s_dev, bits: np.ndarray, seed: int):
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    dr = synth.lwe_draws(seed, len(bits), synth.Params(n=p.n))
+    mu = np.where(bits == 1, 1 << 29, (1 << 32) - (1 << 29)).astype(np.uint32)
+    ct = torch.empty(len(bits), p.n + 1, dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_encrypt(p.n, s_dev, _dev(dr.mask), _dev(dr.noise), _dev(mu), ct, len(bits))
+    return ct
+
+
+def _keys_for(n: int):
+    """Device keys for LWE dimension n (seed 0), loaded into a fresh context."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    p = locpir.params_default()
+    p.n = n
+    d = synth.key_draws(0, synth.Params(n=n))
+    bsk = torch.empty(p.n * 6 * 2 * p.N, dtype=torch.int32, device="cuda")
+    ksk = torch.empty(p.N * 8 * 4 * (p.n + 1), dtype=torch.int32, device="cuda")
+    s_dev = _dev(d.s)
+    locpir.lp_client_keygen_bsk(p, s_dev, _dev(d.S), _dev(d.bsk_mask), _dev(d.bsk_noise), bsk)
+    locpir.lp_client_keygen_ksk(p, s_dev, _dev(d.S), _dev(d.ksk_mask), _dev(d.ksk_noise), ksk)
+    ctx = locpir.Context(0, p)
+    ctx.lp_load_bsk_device(bsk)
+    ctx.lp_load_ksk_device(ksk)
+    return ctx, p, s_dev
+
+
+def _timed(fn, reps: int = 3) -> float:
+    """Median seconds of `reps` runs of fn after one untimed run (which sizes the scratch)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(ts))
+
+
+def paper_shapes() -> None:
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "table1.json")))["rows"]
+    m = 9
+    # Table 2: m = B_x = 9 over Table 1's cities; l = 13 (4 fraction bits) and 16 (7 bits);
+    # 80-bit (n = 540) and 128-bit (n = 630) LWE dimensions.  The point is Seoul's centre.
+    for n in (540, 630):
+        ctx, p, s_dev = _keys_for(n)
+        W = p.n + 1
+        for l in (13, 16):
+            frac = l - 9
+            enc = lambda v: synth.int_to_bits(v, l)
+            boxes = [tuple(_fixed(r[k], frac) for k in ("lat1", "lat2", "lon1", "lon2")) for r in table]
+            px = _fixed((table[0]["lat1"] + table[0]["lat2"]) / 2, frac)
+            py = _fixed((table[0]["lon1"] + table[0]["lon2"]) / 2, frac)
+            bits = np.concatenate([enc(px), enc(py)] + [enc(v) for b in boxes for v in b] +
+                                  [synth.int_to_bits(r["service"], m) for r in table])
+            ct = _encrypt_bits(p, s_dev, bits, 7)
+            x, y = ct[:l], ct[l:2 * l]
+            bx = ct[2 * l:2 * l + 36 * l]
+            sv = ct[2 * l + 36 * l:]
+            out = torch.empty(m, W, dtype=torch.int32, device="cuda")
+            run = lambda: ctx.lp_locpir_query(l, 1, x, y, 9, bx, m, sv, locpir.LP_XOR_CHAIN, out)
+            total = _timed(run)
+            # Phases, each batch timed on its own, with the gate counts and depths of the query's own
+            # phases: the 36 comparators (4 per box) as one batch (LT(a, b) = NOT LE(b, a), and NOT
+            # costs no bootstrap), validation (3 ANDs per box, 2 levels), services (9 x 9 bitwise
+            # AND) and the 8 levels of the XOR chain.
+            cx1 = bx.view(9, 4, l, W)
+            pt = torch.cat([x.expand(9, l, W), y.expand(9, l, W)]).reshape(-1, W)
+            a_le = torch.cat([cx1[:, 0], cx1[:, 2], cx1[:, 1], cx1[:, 3]]).reshape(-1, W).contiguous()
+            b_le = torch.cat([pt, pt]).contiguous()
+            cmp_out = torch.empty(36, W, dtype=torch.int32, device="cuda")
+            t_cmp = _timed(lambda: ctx.lp_compare_batch(locpir.LP_LE, 1, l, a_le, b_le, cmp_out, 36))
+            # The phase inputs are real encryptions of random bits: a zero or garbage mask would
+            # let the blind rotation skip its steps (abar_i = 0) and time too little work.
+            g = _encrypt_bits(p, s_dev, synth.bits(9, 1, 27), 9)
+            t_val = _timed(lambda: (ctx.lp_gate_batch(locpir.LP_AND, g[:18], g[9:27], None, g[:18].clone(), 18),
+                                    ctx.lp_gate_batch(locpir.LP_AND, g[:9], g[9:18], None, g[18:27].clone(), 9)))
+            svc = _encrypt_bits(p, s_dev, synth.bits(9, 2, 81), 10)
+            t_svc = _timed(lambda: ctx.lp_gate_batch(locpir.LP_AND, svc, svc, None, svc.clone(), 81))
+            t_xor = _timed(lambda: [ctx.lp_gate_batch(locpir.LP_XOR, svc[:9], svc[9:18], None, svc[18:27].clone(), 9)
+                                    for _ in range(8)])
+            ph = torch.empty(m, dtype=torch.int32, device="cuda")
+            locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, m)
+            got = sum(int(b > 0) << j for j, b in enumerate(ph.cpu().numpy()))
+            print(json.dumps({"experiment": "table2", "n": n, "l": l, "m": m, "boxes": 9, "seconds_total": total,
+                              "seconds_comparison": t_cmp, "seconds_validation": t_val,
+                              "seconds_service_and": t_svc, "seconds_addxor_chain": t_xor,
+                              "result": got, "expected": table[0]["service"],
+                              "paper_seconds_total": {(540, 13): 4.36, (630, 13): 4.88, (540, 16): 5.12,
+                                                      (630, 16): 5.67}[(n, l)],
+                              "paper_hardware": "Ryzen 5 3500X, TFHE library v1.1 (Table 2)"}), flush=True)
+        if n == 630:
+            # Fig. 4(a): B_x = 10, m = 9, l in {8, 16, 24, 32}; unsigned random boxes.
+            for l in (8, 16, 24, 32):
+                rng = synth.splitmix64(4, 77 + l, 64)
+                bb = []
+                for b in range(10):
+                    a, c = sorted(int(v) % (1 << l) for v in rng[4 * b:4 * b + 2])
+                    d, e = sorted(int(v) % (1 << l) for v in rng[4 * b + 2:4 * b + 4])
+                    bb.append((a, c + 1, d, e + 1))
+                bits = np.concatenate([synth.int_to_bits(int(rng[60]) % (1 << l), l),
+                                       synth.int_to_bits(int(rng[61]) % (1 << l), l)] +
+                                      [synth.int_to_bits(v % (1 << l), l) for b in bb for v in b] +
+                                      [synth.bits(4, 500 + b, m) for b in range(10)])
+                ct = _encrypt_bits(p, s_dev, bits, 8)
+                out = torch.empty(m, W, dtype=torch.int32, device="cuda")
+                run = lambda: ctx.lp_locpir_query(l, 0, ct[:l], ct[l:2 * l], 10, ct[2 * l:42 * l], m, ct[42 * l:],
+                                                  locpir.LP_XOR_TREE, out)
+                print(json.dumps({"experiment": "fig4a", "l": l, "boxes": 10, "m": m, "seconds": _timed(run),
+                                  "paper_seconds": {8: 3.256, 16: 6.139, 24: 8.764, 32: 11.670}[l],
+                                  "paper_hardware": "Ryzen 5 3500X, 6 threads (Section 6.2)"}), flush=True)
+            # Server-known bounds (beyond the paper) against encrypted bounds, same city batch.
+            for nq in (152, 608):
+                print(json.dumps(known_bounds_throughput(ctx, p, s_dev, nq)), flush=True)
+            # Fig. 5's parallel width on the GPU: queries per batch (city shape) -> queries/s.
+            for nq in (1, 8, 64, 152, 304):
+                r = locpir_throughput(ctx, p, s_dev, nq, seed=3)
+                print(json.dumps({"experiment": "batch_width", "queries": nq, "queries_per_s": r["queries_per_s"],
+                                  "seconds": r["seconds"], "wrong_bits": r["wrong_bits"]}), flush=True)
+        ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Serving: Poisson arrivals into the query server (continuous batching).
+# ---------------------------------------------------------------------------------------
+def serve(args) -> None:
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    ctx, p, s_dev, _, _ = setup_gpu(0, count=1)
+    W = p.n + 1
+    rng = np.random.default_rng(4)
+    if args.serve_shape == "uneven":
+        # config-3 distribution: B_x ~ U{1..128}, l ~ U{16, 24, 32}, m = 512
+        protos = synth.multibox_batch(4, args.serve_distinct, m=512)
+        specs = [(q.l, q.x, q.y, q.boxes, q.services) for q in protos]
+    else:
+        protos = synth.city_batch(4, args.serve_distinct, 32, 256)
+        specs = [(32, q.x, q.y, [q.box], q.service[None, :]) for q in protos]
+    queries, expect = [], []
+    for k, (l, x, y, boxes, services) in enumerate(specs):
+        bits = np.concatenate([synth.int_to_bits(x, l), synth.int_to_bits(y, l)] +
+                              [synth.int_to_bits(v, l) for b in boxes for v in b] +
+                              [np.asarray(services, np.uint8).reshape(-1)])
+        ct = _encrypt_bits(p, s_dev, bits, 40 + k)
+        nb, m = len(boxes), np.asarray(services).shape[-1]
+        queries.append(dict(l=l, is_signed=0, n_boxes=nb, m=m, comb=locpir.LP_XOR_TREE, x=ct[:l], y=ct[l:2 * l],
+                            boxes=ct[2 * l:2 * l + 4 * l * nb], services=ct[2 * l + 4 * l * nb:]))
+        # plaintext truth: XOR of the services of the boxes holding the point (X1 <= x < X2, Y1 <= y < Y2)
+        e = np.zeros(m, np.uint8)
+        for (x1, x2, y1, y2), sv in zip(boxes, np.asarray(services, np.uint8).reshape(nb, m)):
+            if x1 <= x < x2 and y1 <= y < y2:
+                e ^= sv
+        expect.append(e)
+    torch.cuda.synchronize()
+    ctx.lp_server_start(int(args.serve_budget_gb * 2**30))
+    tickets, t0 = [], time.perf_counter()
+    next_t = t0
+    try:
+        while True:
+            now = time.perf_counter()
+            if now - t0 >= args.serve_seconds:
+                break
+            if now >= next_t:
+                k = len(tickets) % len(queries)
+                q = dict(queries[k])
+                q["out_service"] = torch.empty(q["m"], W, dtype=torch.int32, device="cuda")
+                try:
+                    tickets.append((ctx.lp_server_submit(q), k, q["out_service"]))
+                except locpir.LocpirError:
+                    pass
+                next_t += rng.exponential(1.0 / args.serve_rate)
+            else:
+                time.sleep(min(next_t - now, 0.01))
+        deadline = time.perf_counter() + args.serve_drain
+        while time.perf_counter() < deadline and not all(ctx.lp_server_poll(t) for t, _, _ in tickets):
+            time.sleep(0.05)
+        st = ctx.lp_server_stats()
+        done = [(k, o) for t, k, o in tickets if ctx.lp_server_poll(t)]
+    finally:
+        ctx.lp_server_stop()
+    wrong = 0
+    for k, o in done:
+        ph = torch.empty(o.shape[0], dtype=torch.int32, device="cuda")
+        locpir.lp_client_lwe_phase(p.n, s_dev, o, ph, o.shape[0])
+        wrong += int(((ph.cpu().numpy() > 0).astype(np.uint8) != expect[k]).sum())
+    print(json.dumps({"experiment": "serving", "shape": args.serve_shape, "arrival_rate_per_s": args.serve_rate,
+                      "arrival_seconds": args.serve_seconds, "drain_seconds": args.serve_drain,
+                      "memory_budget_gb": args.serve_budget_gb, "distinct_queries": len(queries),
+                      "submitted": st["submitted"], "admitted": st["admitted"], "completed": st["completed"],
+                      "rejected": st["rejected"], "still_waiting": st["waiting"], "still_active": st["active"],
+                      "sustained_queries_per_s": st["queries_per_s"], "bootstraps": st["bootstraps"],
+                      "bootstraps_per_s": st["bootstraps_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                      "mean_ms": st["mean_ms"], "ticks": st["ticks"], "checked_queries": len(done),
+                      "wrong_bits": wrong}), flush=True)
 
 
 def run_reference(args) -> None:
@@ -416,11 +674,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--locpir-queries", type=int, default=152,
                     help="LocPIR queries of the city-batch shape timed for queries/s (0: skip)")
+    ap.add_argument("--paper-shapes", action="store_true",
+                    help="run the paper's experiment shapes (Table 2, Fig. 4(a), batch width); one JSON line each")
+    ap.add_argument("--serve", action="store_true", help="serving run: Poisson arrivals into the query server")
+    ap.add_argument("--serve-shape", default="uneven", choices=["uneven", "city"])
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-drain", type=float, default=30.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=4.0)
+    ap.add_argument("--serve-distinct", type=int, default=4)
     ap.add_argument("--count", type=int, default=COUNT,
                     help="gates per step (default 65,536; smaller values are for profiling only)")
     args = ap.parse_args()
     COUNT = args.count
-    if args.impl == "reference":
+    if args.paper_shapes:
+        paper_shapes()
+    elif args.serve:
+        serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -183,6 +183,33 @@ typedef struct lp_query {
 } lp_query;
 int lp_locpir_batch(lp_ctx *ctx, const lp_query *q, size_t nq, void *stream);
 
+/* ---- server-known box bounds (beyond the paper) ------------------------------------------
+ * When the server holds the box bounds in the clear, Algorithm 2's second operand is a known
+ * bit string: XNOR with a known bit is the point bit or its negation (no bootstrap), and the
+ * MUX with a known arm is one AND (bound bit 0) or one OR (bound bit 1) of the negated point
+ * bit with the running result, so a comparator costs at most l - 1 bootstraps instead of 3l.
+ * While the running result is still a known constant no gate is made.
+ *
+ * lp_compare_known_batch: x [count][l][n + 1] (LSB first, device), k [count] plaintext
+ * bounds (host, low l bits used as the bit pattern; with is_signed they are two's
+ * complement); out [count][n + 1] encrypts x < k (LP_LT) or k <= x (LP_LE, the negation).
+ * A comparison whose result is known without a gate (e.g. unsigned x < 0) is written as
+ * the trivial encryption of that bit. */
+int lp_compare_known_batch(lp_ctx *ctx, int kind, int is_signed, int l, const uint32_t *x, const uint64_t *k,
+                           uint32_t *out, size_t count, void *stream);
+
+/* LocPIR queries with known bounds: as lp_query, but bounds [n_boxes][4] (X1, X2, Y1, Y2;
+ * host memory, read during the call) replace the encrypted boxes.  The point is inside a box
+ * iff X1 <= x < X2 and Y1 <= y < Y2; validation, bitwiseAND and the combine are Algorithm 3's. */
+typedef struct lp_query_known {
+    int l, is_signed, n_boxes, m, comb;
+    const uint32_t *x, *y;
+    const uint64_t *bounds;
+    const uint32_t *services;
+    uint32_t *out_service;
+} lp_query_known;
+int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void *stream);
+
 /* Plans: lp_plan_locpir schedules a batch of queries once (levels, job records, a plan-owned
  * pool and scratch) and captures the whole evaluation -- input copies from the queries' pointers,
  * every level's pre-combination / blind-rotation / key-switch pass, output copies -- into one
@@ -210,8 +237,9 @@ int lp_plan_destroy(lp_plan *plan);
  * query is done; *ticket identifies it.  A query larger than the whole budget returns LP_EBUSY.
  * lp_server_poll: *done = 1 once out_service holds the result.  lp_server_wait: block up to
  * timeout_ms (LP_ETIMEOUT).  lp_server_stats: counters and latency percentiles of completed
- * queries (submit -> result on the device).  lp_server_stop: finish the admitted queries, stop
- * the thread, free the pool. */
+ * queries (submit -> result on the device).  lp_server_stop: stop after the tick in flight,
+ * abandoning unfinished queries (their out_service is not written; poll keeps reporting not
+ * done), join the thread and free the pool. */
 #define LP_SERVER_QUEUE 0
 #define LP_SERVER_REJECT 1
 typedef struct lp_stats {

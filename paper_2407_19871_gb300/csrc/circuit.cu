@@ -273,6 +273,58 @@ extern "C" int lp_locpir_query(lp_ctx *c, int l, int is_signed, const uint32_t *
 }
 
 // ---------------------------------------------------------------------------------
+// Server-known bounds (beyond the paper).
+// ---------------------------------------------------------------------------------
+extern "C" int lp_compare_known_batch(lp_ctx *c, int kind, int is_signed, int l, const uint32_t *x, const uint64_t *k,
+                                      uint32_t *out, size_t count, void *stream)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (kind != LP_LT && kind != LP_LE) return fail(LP_EINVAL, "unknown comparison %d", kind);
+    if (l < 1 || l > 64) return fail(LP_EINVAL, "bit width l=%d outside [1, 64]", l);
+    if (count == 0) return LP_OK;
+    if (!x || !k || !out) return fail(LP_EINVAL, "null pointer");
+    const size_t W = (size_t)c->params.n + 1;
+    Circuit C;
+    std::vector<InputCopy> ins;
+    std::vector<OutputCopy> outs;
+    const int a = C.inputs((int)(count * l));
+    ins.push_back(InputCopy{a, x, (int)(count * l)});
+    for (size_t g = 0; g < count; g++) {
+        const Sig s = comp_s_known(C, a + (int)g * l, k[g], l, is_signed != 0);
+        outs.push_back(OutputCopy{kind == LP_LT ? s : Circuit::NOT(s), out + g * W});
+    }
+    return execute(c, C, ins, outs, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int lp_locpir_known_batch(lp_ctx *c, const lp_query_known *q, size_t nq, void *stream)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (nq == 0) return LP_OK;
+    if (!q) return fail(LP_EINVAL, "null query array");
+    const size_t W = (size_t)c->params.n + 1;
+    Circuit C;
+    std::vector<InputCopy> ins;
+    std::vector<OutputCopy> outs;
+    for (size_t i = 0; i < nq; i++) {
+        const lp_query_known &Q = q[i];
+        // Same argument rules as an encrypted-bounds query (the bounds pointer stands in for boxes).
+        lp_query chk{Q.l, Q.is_signed, Q.n_boxes, Q.m, Q.comb, Q.x, Q.y, reinterpret_cast<const uint32_t *>(Q.bounds),
+                     Q.services, Q.out_service};
+        if ((rc = check_query(chk))) return rc;
+        const int x = C.inputs(Q.l), y = C.inputs(Q.l);
+        const int sv = C.inputs(Q.m * Q.n_boxes);
+        ins.push_back(InputCopy{x, Q.x, Q.l});
+        ins.push_back(InputCopy{y, Q.y, Q.l});
+        ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
+        std::vector<Sig> S = build_locpir_known(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, Q.bounds, Q.m, sv, Q.comb);
+        for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{S[j], Q.out_service + (size_t)j * W});
+    }
+    return execute(c, C, ins, outs, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------------
 // Plans: a LocPIR batch scheduled once and captured into a CUDA graph.
 // ---------------------------------------------------------------------------------
 struct lp_plan {

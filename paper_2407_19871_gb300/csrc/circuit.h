@@ -82,6 +82,82 @@ inline Sig comp_le(Circuit &C, int a, int b, int l, bool is_signed)
     return Circuit::NOT(comp_s(C, b, a, l, is_signed));
 }
 
+// Comparator x < K with K known in the clear (beyond the paper): Algorithm 2 with c2's bits
+// known.  XNOR(a, k) is a (k = 1) or NOT a (k = 0); MUX(t1, t0, k) = t1 ? t0 : k becomes
+// AND(NOT a, t0) for k = 0 and OR(NOT a, t0) for k = 1.  While t0 is a known constant c, a
+// step keeps c when k = c and yields NOT a otherwise, without a gate.
+inline Sig comp_s_known(Circuit &C, int c1, uint64_t K, int l, bool is_signed)
+{
+    const int cst = 0;
+    bool known = true;
+    Sig t0;
+    for (int i = 0; i < l; i++) {
+        Sig a{c1 + i, false};
+        int k = (int)((K >> i) & 1u);
+        if (is_signed && i == l - 1) {
+            a = Circuit::NOT(a);
+            k ^= 1;
+        }
+        const Sig na = Circuit::NOT(a);
+        if (known) {
+            if (k != cst) {
+                t0 = na;
+                known = false;
+            }
+        } else {
+            t0 = C.gate(k ? LP_OR : LP_AND, na, t0);
+        }
+    }
+    return known ? Sig{C.zero().w, cst != 0} : t0;
+}
+
+// The combine of the per-box services (Algorithm 4): XOR chain as printed, or a pairwise
+// XOR / OR tree over boxes.
+inline std::vector<Sig> build_locpir_rows(Circuit &C, std::vector<std::vector<Sig>> &rows, int m, int comb)
+{
+    if (comb == LP_XOR_CHAIN) {  // Algorithm 4 as printed (its S_i[j] target read as S[j])
+        std::vector<Sig> S(m, C.zero());
+        for (auto &Si : rows)
+            for (int j = 0; j < m; j++) S[j] = C.gate(LP_XOR, S[j], Si[j]);
+        return S;
+    }
+    const int op = comb == LP_OR_TREE ? LP_OR : LP_XOR;
+    while (rows.size() > 1) {
+        std::vector<std::vector<Sig>> next;
+        for (size_t i = 0; i + 1 < rows.size(); i += 2) {
+            std::vector<Sig> r(m);
+            for (int j = 0; j < m; j++) r[j] = C.gate(op, rows[i][j], rows[i + 1][j]);
+            next.push_back(std::move(r));
+        }
+        if (rows.size() % 2) next.push_back(std::move(rows.back()));
+        rows.swap(next);
+    }
+    return rows[0];
+}
+
+// LocPIR (Algorithm 3) with known bounds [n_boxes][4] = (X1, X2, Y1, Y2): X1 <= x is
+// NOT(x < X1), x < X2 is comp_s_known; validation, bitwiseAND and combine as build_locpir.
+inline std::vector<Sig> build_locpir_known(Circuit &C, int l, bool is_signed, int x, int y, int n_boxes,
+                                           const uint64_t *bounds, int m, int services, int comb)
+{
+    std::vector<std::vector<Sig>> rows;
+    rows.reserve(n_boxes);
+    for (int i = 0; i < n_boxes; i++) {
+        const uint64_t *b = bounds + 4 * (size_t)i;
+        Sig xl = Circuit::NOT(comp_s_known(C, x, b[0], l, is_signed));
+        Sig xr = comp_s_known(C, x, b[1], l, is_signed);
+        Sig yl = Circuit::NOT(comp_s_known(C, y, b[2], l, is_signed));
+        Sig yr = comp_s_known(C, y, b[3], l, is_signed);
+        Sig v1 = C.gate(LP_AND, xl, xr);
+        Sig v2 = C.gate(LP_AND, yl, yr);
+        Sig f = C.gate(LP_AND, v1, v2);
+        std::vector<Sig> Si(m);
+        for (int j = 0; j < m; j++) Si[j] = C.gate(LP_AND, f, Sig{services + i * m + j, false});  // Algorithm 5
+        rows.push_back(std::move(Si));
+    }
+    return build_locpir_rows(C, rows, m, comb);
+}
+
 // LocPIR (Algorithm 3) for one query; x, y, boxes, services are first input wires.
 inline std::vector<Sig> build_locpir(Circuit &C, int l, bool is_signed, int x, int y, int n_boxes, int boxes, int m,
                                      int services, int comb)
@@ -102,24 +178,7 @@ inline std::vector<Sig> build_locpir(Circuit &C, int l, bool is_signed, int x, i
         for (int j = 0; j < m; j++) Si[j] = C.gate(LP_AND, f, Sig{services + i * m + j, false});  // Algorithm 5
         rows.push_back(std::move(Si));
     }
-    if (comb == LP_XOR_CHAIN) {  // Algorithm 4 as printed (its S_i[j] target read as S[j])
-        std::vector<Sig> S(m, C.zero());
-        for (auto &Si : rows)
-            for (int j = 0; j < m; j++) S[j] = C.gate(LP_XOR, S[j], Si[j]);
-        return S;
-    }
-    const int op = comb == LP_OR_TREE ? LP_OR : LP_XOR;
-    while (rows.size() > 1) {
-        std::vector<std::vector<Sig>> next;
-        for (size_t i = 0; i + 1 < rows.size(); i += 2) {
-            std::vector<Sig> r(m);
-            for (int j = 0; j < m; j++) r[j] = C.gate(op, rows[i][j], rows[i + 1][j]);
-            next.push_back(std::move(r));
-        }
-        if (rows.size() % 2) next.push_back(std::move(rows.back()));
-        rows.swap(next);
-    }
-    return rows[0];
+    return build_locpir_rows(C, rows, m, comb);
 }
 
 // Pre-combination of a two-input gate (LocPIR Section 2.2; the TFHE gates it refers to).

@@ -10,7 +10,8 @@
 // its latency (submit -> result on the device) recorded.
 //
 // A gate's output depends only on its input ciphertexts and the keys, so every result is
-// bit-identical to the same query evaluated alone.
+// bit-identical to the same query evaluated alone.  lp_server_stop ends the loop after the tick
+// in flight; queries not finished by then are abandoned (their results are never written).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -257,7 +258,7 @@ static void server_loop(Server *Sp)
                 S.active.push_back(Q);
                 S.admitted++;
             }
-            if (S.stop && (S.active.empty() || S.error)) break;
+            if (S.stop) break;
             if (S.active.empty()) {
                 S.cv.wait_for(lock, std::chrono::milliseconds(20));
                 continue;

@@ -26,7 +26,7 @@ EXPORTS = [
     "lp_params_default", "lp_create", "lp_destroy", "lp_sync", "lp_strerror", "lp_last_error",
     "lp_load_bsk", "lp_load_bsk_device", "lp_load_ksk", "lp_load_ksk_device",
     "lp_gate_batch", "lp_gate_batch_host", "lp_gate_batch_noalloc", "lp_bootstrap_extract", "lp_key_switch",
-    "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch",
+    "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch", "lp_compare_known_batch", "lp_locpir_known_batch",
     "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
     "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
     "lp_preprocess_services", "lp_selftest_wait_timeout",
@@ -44,6 +44,12 @@ class lp_params(ctypes.Structure):
 class lp_query(ctypes.Structure):
     _fields_ = [("l", ctypes.c_int), ("is_signed", ctypes.c_int), ("n_boxes", ctypes.c_int), ("m", ctypes.c_int),
                 ("comb", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("boxes", ctypes.c_void_p),
+                ("services", ctypes.c_void_p), ("out_service", ctypes.c_void_p)]
+
+
+class lp_query_known(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("is_signed", ctypes.c_int), ("n_boxes", ctypes.c_int), ("m", ctypes.c_int),
+                ("comb", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("bounds", ctypes.c_void_p),
                 ("services", ctypes.c_void_p), ("out_service", ctypes.c_void_p)]
 
 
@@ -91,6 +97,8 @@ def lib() -> ctypes.CDLL:
             "lp_compare_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
             "lp_locpir_query": (i, [vp, i, i, vp, vp, i, vp, i, vp, i, vp, vp]),
             "lp_locpir_batch": (i, [vp, ctypes.POINTER(lp_query), sz, vp]),
+            "lp_compare_known_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
+            "lp_locpir_known_batch": (i, [vp, ctypes.POINTER(lp_query_known), sz, vp]),
             "lp_client_lwe_encrypt": (i, [i, vp, vp, vp, vp, vp, sz, vp]),
             "lp_client_lwe_phase": (i, [i, vp, vp, vp, sz, vp]),
             "lp_client_keygen_bsk": (i, [P, vp, vp, vp, vp, vp, vp]),
@@ -334,6 +342,35 @@ class Context:
         for i, q in enumerate(queries):
             arr[i] = self._query_struct(q)
         _check(lib().lp_locpir_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_batch")
+
+    # ---- server-known bounds (beyond the paper)
+    def lp_compare_known_batch(self, kind: int, is_signed: int, l: int, x, k, out, count: int, stream=None) -> None:
+        """x: device ciphertexts [count][l][n+1]; k: plaintext bounds (sequence of count ints)."""
+        W = self.n + 1
+        kb = np.ascontiguousarray(np.asarray(k, dtype=np.uint64).reshape(-1))
+        if kb.size < count:
+            raise ValueError(f"k has {kb.size} bounds, the call reads {count}")
+        _check(lib().lp_compare_known_batch(self.h, kind, is_signed, l, _dptr(x, count * l * W, "x"),
+                                            kb.ctypes.data, _dptr(out, count * W, "out"), count, _stream(stream)),
+               "lp_compare_known_batch")
+
+    def lp_locpir_known_batch(self, queries: list[dict], stream=None) -> None:
+        """queries: dicts with l, is_signed, n_boxes, m, comb, bounds ([n_boxes][4] ints
+        X1, X2, Y1, Y2) and tensors x, y, services, out_service."""
+        W = self.n + 1
+        arr = (lp_query_known * len(queries))()
+        keep = []
+        for i, q in enumerate(queries):
+            l, nb, m = q["l"], q["n_boxes"], q["m"]
+            b = np.ascontiguousarray(np.asarray(q["bounds"], dtype=np.uint64).reshape(-1))
+            if b.size < 4 * nb:
+                raise ValueError(f"bounds has {b.size} values, the query reads {4 * nb}")
+            keep.append(b)
+            arr[i] = lp_query_known(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
+                                    _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"), b.ctypes.data,
+                                    _dptr(q["services"], nb * m * W, "services"),
+                                    _dptr(q["out_service"], m * W, "out_service"))
+        _check(lib().lp_locpir_known_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_known_batch")
 
     # ---- plans (CUDA graphs)
     def lp_plan_locpir(self, queries: list[dict]) -> "Plan":
