@@ -257,6 +257,63 @@ def known_bounds_throughput(ctx, p, s_dev, nq: int, seed: int = 5) -> dict:
             "wrong_bits": wrong}
 
 
+def engines_bench(count: int, ks_count: int) -> None:
+    """Head-to-head of the product engines on NAND gates: the NTT blind rotation against the
+    bf16 and int8 Toeplitz GEMM engines (count gates each), and the digit-pair table key switch
+    against the int8 one-hot GEMM (ks_count gates).  Per engine: bootstraps/s from the library's
+    CUDA events around its blind-rotation (or key-switch) work, the GEMM rate that implies, and
+    the decrypted outputs checked.  Prints one JSON line per engine."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    n = 630
+    # GEMM operations per blind rotation: per CMux step 2 M (K + (W - 1) 2K), M = 2N, K = 6N.
+    M, K = 2048, 6144
+    gemm_ops = {1: 2 * M * (K + 5 * 2 * K) * n, 2: 2 * M * (K + 3 * 2 * K) * n}
+    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(0, count=max(count, ks_count))
+    out = torch.empty_like(a)
+    for br, name in ((0, "ntt"), (1, "tensor_bf16"), (2, "tensor_int8")):
+        ctx.lp_set_engines(br, 0)
+        ctx.lp_gate_batch(locpir.LP_NAND, a[:8], b[:8], None, out[:8], 8)   # warm-up (cuBLAS, scratch)
+        ctx.lp_sync()
+        ctx.lp_set_timing(True)
+        ctx.lp_reset_timing()
+        ctx.lp_gate_batch(locpir.LP_NAND, a[:count], b[:count], None, out[:count], count)
+        ctx.lp_sync()
+        ms, _ = ctx.lp_kernel_time("br")
+        ctx.lp_set_timing(False)
+        wrong = check_outputs(p, s_dev, out[:count], A[:count], B[:count])
+        line = {"experiment": "engines", "stage": "blind_rotation", "engine": name, "gates": count,
+                "ms": ms, "bootstraps_per_s": count / (ms / 1e3), "decrypt_errors": wrong}
+        if br:
+            ops = gemm_ops[br] * count / (ms / 1e3)
+            line["gemm_rate"] = ops / 1e12
+            line["gemm_unit"] = "TFLOP/s" if br == 1 else "TOPS"
+            if br == 1 and "bf16_tflops" in peaks:
+                line["frac_of_measured_bf16_peak"] = ops / 1e12 / peaks["bf16_tflops"]
+        print(json.dumps(line), flush=True)
+    for ks, name in ((0, "table"), (1, "tensor_int8_onehot")):
+        ctx.lp_set_engines(0, ks)
+        ctx.lp_gate_batch(locpir.LP_NAND, a[:8], b[:8], None, out[:8], 8)
+        ctx.lp_sync()
+        ctx.lp_set_timing(True)
+        ctx.lp_reset_timing()
+        ctx.lp_gate_batch(locpir.LP_NAND, a[:ks_count], b[:ks_count], None, out[:ks_count], ks_count)
+        ctx.lp_sync()
+        ms, _ = ctx.lp_kernel_time("ks")
+        ctx.lp_set_timing(False)
+        wrong = check_outputs(p, s_dev, out[:ks_count], A[:ks_count], B[:ks_count])
+        line = {"experiment": "engines", "stage": "key_switch", "engine": name, "gates": ks_count, "ms": ms,
+                "key_switches_per_s": ks_count / (ms / 1e3), "decrypt_errors": wrong}
+        if ks:
+            line["gemm_rate"] = 2 * 4 * 632 * 24576 * ks_count / (ms / 1e3) / 1e12
+            line["gemm_unit"] = "TOPS"
+        print(json.dumps(line), flush=True)
+    ctx.lp_set_engines(0, 0)
+    ctx.close()
+
+
 def check_outputs(p, s_dev, out, A, B) -> int:
     import torch
     from paper_2407_19871_gb300 import locpir
@@ -677,6 +734,10 @@ def main():
     ap.add_argument("--paper-shapes", action="store_true",
                     help="run the paper's experiment shapes (Table 2, Fig. 4(a), batch width); one JSON line each")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson arrivals into the query server")
+    ap.add_argument("--engines", action="store_true",
+                    help="head-to-head of the NTT and tensor-core (GEMM) engines instead of the bench line")
+    ap.add_argument("--engines-count", type=int, default=4096)
+    ap.add_argument("--engines-ks-count", type=int, default=65536)
     ap.add_argument("--serve-shape", default="uneven", choices=["uneven", "city"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -691,6 +752,8 @@ def main():
         paper_shapes()
     elif args.serve:
         serve(args)
+    elif args.engines:
+        engines_bench(args.engines_count, args.engines_ks_count)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -210,6 +210,25 @@ typedef struct lp_query_known {
 } lp_query_known;
 int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void *stream);
 
+/* ---- alternative product engines (measured against the defaults; beyond the paper) -------
+ * lp_set_engines selects the engines of lp_gate_batch, lp_gate_batch_host,
+ * lp_bootstrap_extract and lp_key_switch (circuits, plans and the server always use the
+ * defaults).  Every engine computes the same exact integers, so outputs are bit-identical.
+ *   LP_BR_NTT          two-prime NTT external products in shared memory (default);
+ *   LP_BR_TENSOR_BF16  per step one Toeplitz(BSK_i) x digit-matrix GEMM on the bf16 tensor
+ *                      cores (cuBLAS), factors split into 6-bit limbs so fp32 sums stay exact;
+ *   LP_BR_TENSOR_INT8  the same with 8-bit limbs on the int8 tensor cores, int32 sums;
+ *   LP_KS_TABLE        digit-pair table gather (default);
+ *   LP_KS_TENSOR_INT8  one-hot digits x KSK limbs as one int8 GEMM per batch.
+ * Returns LP_EINVAL for an unknown engine.  May be called before or after the keys are loaded;
+ * the key layouts an engine needs are built when both are available. */
+#define LP_BR_NTT 0
+#define LP_BR_TENSOR_BF16 1
+#define LP_BR_TENSOR_INT8 2
+#define LP_KS_TABLE 0
+#define LP_KS_TENSOR_INT8 1
+int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
+
 /* Plans: lp_plan_locpir schedules a batch of queries once (levels, job records, a plan-owned
  * pool and scratch) and captures the whole evaluation -- input copies from the queries' pointers,
  * every level's pre-combination / blind-rotation / key-switch pass, output copies -- into one

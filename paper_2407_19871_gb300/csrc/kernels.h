@@ -37,6 +37,8 @@ cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32
 cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
                       const uint32_t *T, int n, int *err, int num_sms, cudaStream_t st);
 cudaError_t launch_ks_table(const uint32_t *ksk, uint32_t *T, int n, int num_sms, cudaStream_t st);
+// Words per key-switch table row and per output ciphertext buffer row: n + 1 rounded up to 4.
+__host__ __device__ __forceinline__ int ks_row_words(int n) { return ((n + 1) + 3) & ~3; }
 __host__ __device__ size_t ks_table_words(int n);
 cudaError_t launch_negate(const uint32_t *in, uint32_t *out, size_t words, int num_sms, cudaStream_t st);
 cudaError_t launch_gather(const uint32_t *pool, const int *slots, const uint8_t *neg, size_t cnt, int n,

@@ -34,7 +34,6 @@ constexpr int KS_CROWS = 16;       // table rows per pair
 constexpr int KS_RING = 3;
 constexpr int KS_ICH = 32;         // input coefficients staged at a time
 
-__host__ __device__ __forceinline__ int ks_row_words(int n) { return ((n + 1) + 3) & ~3; }
 __host__ __device__ size_t ks_table_words(int n) { return (size_t)RING_N * KS_PAIRS * KS_CROWS * ks_row_words(n); }
 
 // Table from the key-switching key [N][t][4][n+1].

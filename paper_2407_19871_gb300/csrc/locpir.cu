@@ -216,8 +216,9 @@ extern "C" int lp_destroy(lp_ctx *c)
             cudaEventDestroy(ev.second);
         }
     }
-    for (DevBuf *b : {&c->tw_lane, &c->err, &c->bsk_hat, &c->ksk, &c->abar, &c->ext, &c->pool, &c->jobs,
-                      &c->tmp_in, &c->tmp_out})
+    tc_release(c);
+    for (DevBuf *b : {&c->tw_lane, &c->err, &c->bsk_hat, &c->bsk_coef, &c->ksk, &c->abar, &c->ext, &c->pool,
+                      &c->jobs, &c->tmp_in, &c->tmp_out})
         free_buf(*b);
     delete c;
     return LP_OK;
@@ -323,25 +324,17 @@ static int load_bsk_common(lp_ctx *c, const uint32_t *src, bool on_device, size_
         return fail(LP_EINVAL, "bootstrapping key has %zu words, expected %zu", words, bsk_words(c->params));
     cudaSetDevice(c->device);
     int rc = ensure_buf(c->bsk_hat, words * 2 * sizeof(uint32_t), "bootstrapping key");
+    // The coefficient-domain key stays resident (31 MB) for the Toeplitz engines.
+    if (!rc) rc = ensure_buf(c->bsk_coef, words * sizeof(uint32_t), "bootstrapping key (coefficients)");
     if (rc) return rc;
-    DevBuf coef;
-    const uint32_t *dsrc = src;
-    if (!on_device) {
-        rc = ensure_buf(coef, words * sizeof(uint32_t), "bootstrapping key staging");
-        if (rc) return rc;
-        cudaError_t e = cudaMemcpyAsync(coef.ptr, src, words * 4, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) {
-            free_buf(coef);
-            return cuda_fail(e, "copy bootstrapping key");
-        }
-        dsrc = static_cast<const uint32_t *>(coef.ptr);
-    }
-    cudaError_t e = launch_bsk_to_ntt(dsrc, static_cast<uint32_t *>(c->bsk_hat.ptr), c->params.n,
-                                      static_cast<const uint2 *>(c->tw_lane.ptr), c->tables.bsk_scale[0],
-                                      c->tables.bsk_scale[1], c->num_sms, st);
+    cudaError_t e = cudaMemcpyAsync(c->bsk_coef.ptr, src, words * 4,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy bootstrapping key");
+    e = launch_bsk_to_ntt(static_cast<const uint32_t *>(c->bsk_coef.ptr), static_cast<uint32_t *>(c->bsk_hat.ptr),
+                          c->params.n, static_cast<const uint2 *>(c->tw_lane.ptr), c->tables.bsk_scale[0],
+                          c->tables.bsk_scale[1], c->num_sms, st);
     c->launches++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    free_buf(coef);
     if (e != cudaSuccess) return cuda_fail(e, "convert bootstrapping key");
     c->have_bsk = true;
     return LP_OK;
@@ -383,6 +376,10 @@ static int load_ksk_common(lp_ctx *c, const uint32_t *src, bool on_device, size_
     free_buf(staging);
     if (e != cudaSuccess) return cuda_fail(e, "build key-switching table");
     c->have_ksk = true;
+    if (c->ks_engine == LP_KS_TENSOR_INT8) {
+        if ((rc = ks_tensor_prepare(c, st))) return rc;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "build one-hot key");
+    }
     return LP_OK;
 }
 
@@ -412,6 +409,11 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
 {
     cudaEvent_t ev0;
     timer_begin(c, "br", st, &ev0);
+    if (c->br_engine != LP_BR_NTT) {
+        const int rc = run_br_tensor(c, jobs, mu, st);
+        timer_end(c, "br", st, ev0);
+        return rc;
+    }
     cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
@@ -426,12 +428,36 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
 {
     cudaEvent_t ev0;
     timer_begin(c, "ks", st, &ev0);
+    if (c->ks_engine != LP_KS_TABLE) {
+        const int rc = run_ks_tensor(c, jobs, njobs, dense_mux, out, st);
+        timer_end(c, "ks", st, ev0);
+        return rc;
+    }
     cudaError_t e = launch_ks(static_cast<const uint32_t *>(c->ext.ptr), jobs, njobs, dense_mux, out,
                               static_cast<const uint32_t *>(c->ksk.ptr), c->params.n,
                               static_cast<int *>(c->err.ptr), c->num_sms, st);
     timer_end(c, "ks", st, ev0);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
+    return LP_OK;
+}
+
+extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (br_engine < LP_BR_NTT || br_engine > LP_BR_TENSOR_INT8)
+        return fail(LP_EINVAL, "unknown blind-rotation engine %d", br_engine);
+    if (ks_engine < LP_KS_TABLE || ks_engine > LP_KS_TENSOR_INT8)
+        return fail(LP_EINVAL, "unknown key-switch engine %d", ks_engine);
+    cudaSetDevice(c->device);
+    if (ks_engine == LP_KS_TENSOR_INT8 && c->have_ksk && !c->ks_A.ptr) {
+        int rc = ks_tensor_prepare(c, 0);
+        if (rc) return rc;
+        const cudaError_t e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) return cuda_fail(e, "build one-hot key");
+    }
+    c->br_engine = br_engine;
+    c->ks_engine = ks_engine;
     return LP_OK;
 }
 

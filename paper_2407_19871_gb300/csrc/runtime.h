@@ -40,6 +40,11 @@ struct lp_ctx {
     uint64_t launches = 0;
     std::map<std::string, lp::KernelTimer> timers;
     lp::Server *server = nullptr;   // query server (lp_server_start), if running
+    // Alternative tensor-core engines (tensor_engine.cu) and their state.
+    int br_engine = LP_BR_NTT, ks_engine = LP_KS_TABLE;
+    void *blas = nullptr;           // cuBLAS handle, created on first use
+    lp::DevBuf bsk_coef;            // coefficient-domain BSK (Toeplitz engine)
+    lp::DevBuf tc_T, tc_D, tc_C, tc_acc, ks_A, ks_H, ks_C, ks_aux;
 };
 
 namespace lp {
@@ -53,6 +58,10 @@ int abar_stride(const lp_ctx *c);
 int ensure_scratch(lp_ctx *c, size_t br_jobs);
 int run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);
 int run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);
+int run_br_tensor(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);
+int run_ks_tensor(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);
+int ks_tensor_prepare(lp_ctx *c, cudaStream_t st);
+void tc_release(lp_ctx *c);
 void timer_begin(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t *ev0);
 void timer_end(lp_ctx *c, const char *name, cudaStream_t st, cudaEvent_t ev0);
 

@@ -32,8 +32,10 @@ EXPORTS = [
     "lp_preprocess_services", "lp_selftest_wait_timeout",
     "lp_server_start", "lp_server_submit", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
-    "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy",
+    "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines",
 ]
+LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8 = 0, 1, 2
+LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
 LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
 
 
@@ -125,6 +127,7 @@ def lib() -> ctypes.CDLL:
             "lp_plan_info": (i, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)]),
             "lp_plan_destroy": (i, [vp]),
+            "lp_set_engines": (i, [vp, i, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -342,6 +345,10 @@ class Context:
         for i, q in enumerate(queries):
             arr[i] = self._query_struct(q)
         _check(lib().lp_locpir_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_batch")
+
+    # ---- alternative product engines
+    def lp_set_engines(self, br_engine: int = LP_BR_NTT, ks_engine: int = LP_KS_TABLE) -> None:
+        _check(lib().lp_set_engines(self.h, br_engine, ks_engine), "lp_set_engines")
 
     # ---- server-known bounds (beyond the paper)
     def lp_compare_known_batch(self, kind: int, is_signed: int, l: int, x, k, out, count: int, stream=None) -> None:
