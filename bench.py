@@ -314,6 +314,37 @@ def engines_bench(count: int, ks_count: int) -> None:
     ctx.close()
 
 
+def br_latency_bench() -> None:
+    """Blind-rotation time per launch against the level width, for the batched kernel (4
+    ciphertexts per CTA) and the split kernel (one ciphertext per CTA over 12 warps): CUDA
+    events around the library's blind-rotation launches, median of 3 after a warm-up, outputs
+    decrypted.  One JSON line per (kernel, width)."""
+    from paper_2407_19871_gb300 import locpir
+    import torch
+    widths = (1, 4, 16, 64, 152, 304, 608, 1216)
+    ctx, p, s_dev, (A, B), (a, b) = setup_gpu(0, count=max(widths))
+    out = torch.empty_like(a)
+    for eng, name in ((locpir.LP_BR_NTT_BATCHED, "batched"), (locpir.LP_BR_NTT_SPLIT, "split")):
+        ctx.lp_set_engines(eng, 0)
+        for w in widths:
+            ctx.lp_gate_batch(locpir.LP_NAND, a[:w], b[:w], None, out[:w], w)
+            ctx.lp_sync()
+            ts = []
+            for _ in range(3):
+                ctx.lp_set_timing(True)
+                ctx.lp_reset_timing()
+                ctx.lp_gate_batch(locpir.LP_NAND, a[:w], b[:w], None, out[:w], w)
+                ctx.lp_sync()
+                ts.append(ctx.lp_kernel_time("br")[0])
+                ctx.lp_set_timing(False)
+            ms = float(np.median(ts))
+            wrong = check_outputs(p, s_dev, out[:w], A[:w], B[:w])
+            print(json.dumps({"experiment": "br_latency", "kernel": name, "ciphertexts": w, "br_ms": ms,
+                              "bootstraps_per_s": w / (ms / 1e3), "decrypt_errors": wrong}), flush=True)
+    ctx.lp_set_engines(0, 0)
+    ctx.close()
+
+
 def check_outputs(p, s_dev, out, A, B) -> int:
     import torch
     from paper_2407_19871_gb300 import locpir
@@ -737,6 +768,8 @@ def main():
     ap.add_argument("--engines", action="store_true",
                     help="head-to-head of the NTT and tensor-core (GEMM) engines instead of the bench line")
     ap.add_argument("--engines-count", type=int, default=4096)
+    ap.add_argument("--br-latency", action="store_true",
+                    help="blind-rotation time against level width, batched and split kernels")
     ap.add_argument("--engines-ks-count", type=int, default=65536)
     ap.add_argument("--serve-shape", default="uneven", choices=["uneven", "city"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -754,6 +787,8 @@ def main():
         serve(args)
     elif args.engines:
         engines_bench(args.engines_count, args.engines_ks_count)
+    elif args.br_latency:
+        br_latency_bench()
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -214,7 +214,12 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
  * lp_set_engines selects the engines of lp_gate_batch, lp_gate_batch_host,
  * lp_bootstrap_extract and lp_key_switch (circuits, plans and the server always use the
  * defaults).  Every engine computes the same exact integers, so outputs are bit-identical.
- *   LP_BR_NTT          two-prime NTT external products in shared memory (default);
+ *   LP_BR_NTT          two-prime NTT external products in shared memory (default): a level
+ *                      of at most two ciphertexts per SM runs split (one ciphertext per CTA,
+ *                      its 12 digit-and-prime transforms on 12 warps: lower latency), a larger
+ *                      one batched (4 ciphertexts per CTA sharing each key row);
+ *   LP_BR_NTT_BATCHED  the NTT engine, always batched;
+ *   LP_BR_NTT_SPLIT    the NTT engine, always split;
  *   LP_BR_TENSOR_BF16  per step one Toeplitz(BSK_i) x digit-matrix GEMM on the bf16 tensor
  *                      cores (cuBLAS), factors split into 6-bit limbs so fp32 sums stay exact;
  *   LP_BR_TENSOR_INT8  the same with 8-bit limbs on the int8 tensor cores, int32 sums;
@@ -225,6 +230,8 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
 #define LP_BR_NTT 0
 #define LP_BR_TENSOR_BF16 1
 #define LP_BR_TENSOR_INT8 2
+#define LP_BR_NTT_BATCHED 3
+#define LP_BR_NTT_SPLIT 4
 #define LP_KS_TABLE 0
 #define LP_KS_TENSOR_INT8 1
 int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);

@@ -333,6 +333,184 @@ __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
 }
 
 // ---------------------------------------------------------------------------------
+// Split blind rotation: one ciphertext per CTA, its external product spread over
+// SPLIT_WARPS = 12 warps, one per (prime, digit row).  It shortens one CMux step about four
+// times against br_kernel (whose warp pair runs all 6 forward and 2 inverse transforms of a
+// ciphertext in sequence), for levels too small to fill the GPU with groups of BR_SLOTS.
+//
+// Per step: every warp rotates/decomposes its own digit row r of ACC, forward-transforms it
+// modulo its prime, multiplies it with its key rows (one Montgomery reduction per product;
+// x < 22p and key < p keep each product below 22 p^2 < 2^32 p, so each reduced product is in
+// [0, 2p)) and adds both output components into the shared partial sums of its prime
+// (shared-memory atomics; 6 terms < 12p < 2^32).  After a barrier, warps (pi, c) for c = 0, 1
+// inverse-transform component c modulo prime pi; after another, all threads recombine both
+// primes (centred CRT) into ACC and clear the partial sums.  Each warp owns an 8 KB key
+// buffer, refilled by its lane 0 with the next step's row right after its MAC (cp.async.bulk,
+// bounded mbarrier wait at the next step).  Steps with abar_i = 0 leave ACC unchanged and
+// are skipped (CTA-uniform), as in br_kernel.
+// ---------------------------------------------------------------------------------
+constexpr int SPLIT_WARPS = 2 * ROWS;
+constexpr int SPLIT_THREADS = SPLIT_WARPS * 32;
+
+struct __align__(16) SplitSmem {
+    uint32_t key[SPLIT_WARPS][CHUNK_WORDS];             // 96 KB: this step's row per warp
+    uint32_t tbuf[SPLIT_WARPS][32 * 33];                 // 50 KB
+    uint2 tw[2][2][LANE_TW * 32];                        // 31 KB [prime][dir]
+    uint32_t part[2][2][RING_N];                         // 16 KB [prime][component]
+    uint32_t acc[2][RING_N];                             // 8 KB
+    uint16_t abar[ABAR_STRIDE_MAX];                      // 2 KB
+    uint64_t bar[SPLIT_WARPS];
+    int abort;
+};
+
+size_t br_split_smem_bytes() { return sizeof(SplitSmem); }
+
+__device__ __forceinline__ void split_issue(SplitSmem &sm, const uint32_t *bsk_hat, int w, int pi, int r, int i)
+{
+    mbar_arrive_expect_tx(&sm.bar[w], CHUNK_BYTES);
+    bulk_copy_g2s(sm.key[w], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + r) * CHUNK_WORDS, CHUNK_BYTES, &sm.bar[w]);
+}
+
+// Partial sums are stored in transform (layout B) order, index 32 lane + k swizzled to
+// 32 lane + (k ^ lane) so that a warp's 32 lanes hit 32 different banks.
+__device__ __forceinline__ int split_pos(int lane, int k) { return lane * 32 + (k ^ lane); }
+
+__global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SplitSmem &sm = *reinterpret_cast<SplitSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pi = warp / ROWS, r = warp % ROWS;
+    const int c_in = r / LG, p_dig = r % LG;
+    const int n = a.n;
+    const PrimeK K = prime_k(pi);
+
+    for (int i = threadIdx.x; i < 2 * 2 * LANE_TW * 32; i += blockDim.x) (&sm.tw[0][0][0])[i] = a.tw_lane[i];
+    for (int i = threadIdx.x; i < 2 * 2 * RING_N; i += blockDim.x) (&sm.part[0][0][0])[i] = 0u;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < SPLIT_WARPS; w++) mbar_init(&sm.bar[w], 1);
+        sm.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    uint32_t *tbuf = sm.tbuf[warp];
+    uint32_t phase = 0;          // completed uses of this warp's barrier
+    bool pending = false;        // a copy into this warp's key buffer is in flight
+    bool aborted = false;
+    for (int job = blockIdx.x; job < a.jobs && !aborted; job += gridDim.x) {
+        const uint16_t *src = a.abar + (size_t)job * a.abar_stride;
+        for (int i = threadIdx.x; i <= n; i += blockDim.x) sm.abar[i] = src[i];
+        __syncthreads();
+        const int bb = sm.abar[n];
+        for (int j = threadIdx.x; j < RING_N; j += blockDim.x) {
+            sm.acc[0][j] = 0u;
+            const int e = (j + bb) & (2 * RING_N - 1);
+            sm.acc[1][j] = (e & RING_N) ? (0u - a.mu) : a.mu;
+        }
+        if (n > 0) {
+            if (lane == 0) split_issue(sm, a.bsk_hat, warp, pi, r, 0);
+            pending = true;   // every lane tracks the barrier phase
+        }
+        __syncthreads();
+        for (int i = 0; i < n; i++) {
+            const int ab = sm.abar[i];
+            // This step's key row has landed (bounded wait); refill happens after the MAC.
+            bool ok = true;
+            if (pending) {
+                ok = mbar_wait_bounded(&sm.bar[warp], phase & 1u, &sm.abort);
+                phase++;
+                pending = false;
+            }
+            if (!ok && lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+            if (ab != 0 && ok) {
+                const uint32_t *A = sm.acc[c_in];
+                const int sh = 32 - BGBIT * (p_dig + 1);
+                uint32_t x[32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    const int j = lane + 32 * k;
+                    const int idx = (j - ab) & (2 * RING_N - 1);
+                    uint32_t v = A[idx & (RING_N - 1)];
+                    v = (idx & RING_N) ? (0u - v) : v;
+                    const uint32_t u = v - A[j] + GADGET_OFF;
+                    x[k] = ((u >> sh) & 1023u) + (K.p - 512u);
+                }
+                ntt_fwd<false>(x, tbuf, sm.tw[pi][0], lane, pi, K);
+                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.key[warp]);
+                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.key[warp] + RING_N);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const uint4 b0 = ch0[q * 32 + lane];
+                    const uint4 b1 = ch1[q * 32 + lane];
+                    const uint32_t bb0[4] = {b0.x, b0.y, b0.z, b0.w};
+                    const uint32_t bb1[4] = {b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int k = 4 * q + e;
+                        atomicAdd(&sm.part[pi][0][split_pos(lane, k)], redc64((unsigned long long)x[k] * bb0[e], K));
+                        atomicAdd(&sm.part[pi][1][split_pos(lane, k)], redc64((unsigned long long)x[k] * bb1[e], K));
+                    }
+                }
+            }
+            // Refill this warp's key buffer with the next step's row (its reads are done).
+            __syncwarp();
+            if (lane == 0 && ok && i + 1 < n) {
+                fence_proxy_async_smem();
+                split_issue(sm, a.bsk_hat, warp, pi, r, i + 1);
+                pending = true;
+            }
+            pending = __shfl_sync(0xffffffffu, pending ? 1 : 0, 0) != 0;
+            if (__syncthreads_or(!ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0)) {
+                aborted = true;
+                break;
+            }
+            if (ab == 0) continue;   // CTA-uniform: ACC unchanged, partial sums still zero
+            if (r < 2) {
+                // Warp (pi, c = r): component c modulo prime pi.  Six terms in [0, 2p) sum below
+                // 12p; three conditional subtractions bring them into [0, 2p).
+                const int c = r;
+                uint32_t y[1][32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    uint32_t v = sm.part[pi][c][split_pos(lane, k)];
+                    v = umin_u32(v, v - 4u * K.p2);
+                    v = umin_u32(v, v - 2u * K.p2);
+                    y[0][k] = umin_u32(v, v - K.p2);
+                }
+                __syncwarp();
+                ntt_inv_multi<1>(y, tbuf, sm.tw[pi][1], lane, pi, K);
+#pragma unroll
+                for (int k = 0; k < 32; k++) sm.part[pi][c][lane + 32 * k] = umin_u32(y[0][k], y[0][k] - K.p);
+            }
+            __syncthreads();
+            // ACC += CRT(residues) for both components; clear the partial sums for the next step.
+            for (int t = threadIdx.x; t < 2 * RING_N; t += blockDim.x) {
+                const int c = t / RING_N, j = t % RING_N;
+                const uint32_t x0 = sm.part[0][c][j], x1 = sm.part[1][c][j];
+                sm.part[0][c][j] = 0u;
+                sm.part[1][c][j] = 0u;
+                sm.acc[c][j] += crt_lift(x0, x1);
+            }
+            __syncthreads();
+        }
+        if (aborted) break;
+        // Sample extraction: a'_0 = A_0, a'_j = -A_{N-j}, b' = B_0.
+        uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
+        for (int j = threadIdx.x; j < RING_N; j += blockDim.x)
+            dst[j] = j == 0 ? sm.acc[0][0] : 0u - sm.acc[0][RING_N - j];
+        if (threadIdx.x == 0) dst[RING_N] = sm.acc[1][0];
+        __syncthreads();
+    }
+    if (aborted && threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    // No bulk copy may still be in flight when the CTA exits (only possible after an abort).
+    if (lane == 0 && pending) {
+        volatile int never = 0;
+        if (!mbar_wait_bounded(&sm.bar[warp], phase & 1u, &never)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Bootstrapping key -> transform domain.  One warp per (i, prime, row, component)
 // polynomial: centred lift mod p, forward NTT, scale by N^-1 2^32 mod p, store in the
 // chunk layout the blind rotation reads (component c, then [q][lane][4] so that lane t
@@ -406,13 +584,25 @@ cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, con
 
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
-                      cudaStream_t st)
+                      cudaStream_t st, int variant)
 {
     if (jobs <= 0) return cudaSuccess;
+    BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
+    // Policy (measured on GB300): a split CTA finishes one ciphertext in 4.4-4.8 ms, a batched
+    // wave of up to 4 per SM takes 13.3-14.3 ms, so levels of up to two ciphertexts per SM run
+    // split (one or two split waves) and larger ones batched.
+    const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= 2 * num_sms);
+    if (split) {
+        const size_t smem = sizeof(SplitSmem);
+        cudaError_t e = cudaFuncSetAttribute(br_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = jobs < num_sms ? jobs : num_sms;
+        br_split_kernel<<<grid, SPLIT_THREADS, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(BrSmem);
     cudaError_t e = cudaFuncSetAttribute(br_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
     const int groups = (jobs + BR_SLOTS - 1) / BR_SLOTS;
     const int grid = groups < num_sms ? groups : num_sms;
     br_kernel<<<grid, BR_THREADS, smem, st>>>(a);

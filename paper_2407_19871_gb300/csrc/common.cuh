@@ -118,6 +118,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         : "memory");
 }
 
+// Orders this thread's earlier generic-proxy shared-memory accesses (and those it has
+// observed) before its later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Named barrier over `threads` threads with an OR-reduction of pred across them.
 __device__ __forceinline__ bool bar_red_or(int id, int threads, bool pred)
 {

@@ -409,15 +409,18 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
 {
     cudaEvent_t ev0;
     timer_begin(c, "br", st, &ev0);
-    if (c->br_engine != LP_BR_NTT) {
+    if (c->br_engine == LP_BR_TENSOR_BF16 || c->br_engine == LP_BR_TENSOR_INT8) {
         const int rc = run_br_tensor(c, jobs, mu, st);
         timer_end(c, "br", st, ev0);
         return rc;
     }
+    const int variant = c->br_engine == LP_BR_NTT_BATCHED ? BR_VARIANT_BATCHED
+                        : c->br_engine == LP_BR_NTT_SPLIT ? BR_VARIANT_SPLIT
+                                                          : BR_VARIANT_AUTO;
     cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
-                              static_cast<int *>(c->err.ptr), c->num_sms, st);
+                              static_cast<int *>(c->err.ptr), c->num_sms, st, variant);
     timer_end(c, "br", st, ev0);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
@@ -445,7 +448,7 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
 extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
 {
     if (!c) return fail(LP_EINVAL, "null context");
-    if (br_engine < LP_BR_NTT || br_engine > LP_BR_TENSOR_INT8)
+    if (br_engine < LP_BR_NTT || br_engine > LP_BR_NTT_SPLIT)
         return fail(LP_EINVAL, "unknown blind-rotation engine %d", br_engine);
     if (ks_engine < LP_KS_TABLE || ks_engine > LP_KS_TENSOR_INT8)
         return fail(LP_EINVAL, "unknown key-switch engine %d", ks_engine);

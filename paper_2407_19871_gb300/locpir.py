@@ -34,7 +34,7 @@ EXPORTS = [
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines",
 ]
-LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8 = 0, 1, 2
+LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
 LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
 

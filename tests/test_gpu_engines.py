@@ -84,6 +84,38 @@ def test_gates_all_engine_pairs_agree(engines_ctx, keys, op):
 def test_unknown_engine_is_rejected(engines_ctx):
     from paper_2407_19871_gb300.locpir import LocpirError
     with pytest.raises(LocpirError):
-        engines_ctx.lp_set_engines(3, 0)
+        engines_ctx.lp_set_engines(5, 0)
     with pytest.raises(LocpirError):
         engines_ctx.lp_set_engines(0, 2)
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_ntt_variants_match_oracle(engines_ctx, keys, variant):
+    """The batched (4 ciphertexts per CTA) and split (12 warps per ciphertext) NTT kernels,
+    forced, on one full group plus a ragged one."""
+    p = keys.params
+    lwe = _random_lwes(61 + variant, 7, p.n)
+    engines_ctx.lp_set_engines(variant, 0)
+    ext = empty_dev(7, p.N + 1)
+    engines_ctx.lp_bootstrap_extract(to_dev(lwe), EIGHTH, ext, 7)
+    engines_ctx.lp_sync()
+    assert_same(to_host(ext), oracle.bootstrap_extract(keys, lwe), f"variant {variant}")
+
+
+def test_split_kernel_beyond_one_wave(engines_ctx, keys):
+    """More ciphertexts than SMs, forced split: CTAs loop over several ciphertexts each.  The
+    split and batched kernels agree on every word, and sampled rows equal the oracle's."""
+    import torch
+    p = keys.params
+    count = 2 * torch.cuda.get_device_properties(0).multi_processor_count + 5
+    lwe = _random_lwes(63, count, p.n)
+    outs = {}
+    for variant in (3, 4):
+        engines_ctx.lp_set_engines(variant, 0)
+        ext = empty_dev(count, p.N + 1)
+        engines_ctx.lp_bootstrap_extract(to_dev(lwe), EIGHTH, ext, count)
+        engines_ctx.lp_sync()
+        outs[variant] = to_host(ext)
+    assert_same(outs[4], outs[3], "split vs batched")
+    rows = [0, count // 2, count - 1]
+    assert_same(outs[4][rows], oracle.bootstrap_extract(keys, lwe[rows]), "split vs oracle (sampled rows)")
