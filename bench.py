@@ -329,18 +329,20 @@ def br_latency_bench() -> None:
         for w in widths:
             ctx.lp_gate_batch(locpir.LP_NAND, a[:w], b[:w], None, out[:w], w)
             ctx.lp_sync()
-            ts = []
+            ts, tk = [], []
             for _ in range(3):
                 ctx.lp_set_timing(True)
                 ctx.lp_reset_timing()
                 ctx.lp_gate_batch(locpir.LP_NAND, a[:w], b[:w], None, out[:w], w)
                 ctx.lp_sync()
                 ts.append(ctx.lp_kernel_time("br")[0])
+                tk.append(ctx.lp_kernel_time("ks")[0])
                 ctx.lp_set_timing(False)
             ms = float(np.median(ts))
             wrong = check_outputs(p, s_dev, out[:w], A[:w], B[:w])
             print(json.dumps({"experiment": "br_latency", "kernel": name, "ciphertexts": w, "br_ms": ms,
-                              "bootstraps_per_s": w / (ms / 1e3), "decrypt_errors": wrong}), flush=True)
+                              "bootstraps_per_s": w / (ms / 1e3), "ks_ms": float(np.median(tk)),
+                              "decrypt_errors": wrong}), flush=True)
     ctx.lp_set_engines(0, 0)
     ctx.close()
 

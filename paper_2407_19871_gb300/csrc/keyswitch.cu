@@ -19,6 +19,14 @@
 // full / empty mbarriers; thread 0 is the producer.  Each warp owns 4 outputs; lane l owns
 // words l + 32 q (q < KS_CPT), so every shared-memory read of the warp is conflict-free.
 // MUX jobs sum their two extracted samples and (0, 1/8) while their inputs are staged.
+//
+// Small batches.  A CTA streams the whole 165.7 MB table once per batch of KS_CT outputs,
+// which takes about 2.5 ms however few outputs there are.  When the batches cannot fill
+// half of the SMs, the input coefficients are split into up to 32 slices (grid.y): every
+// CTA streams only its slice of the table and adds its partial sum into the output words
+// with global atomics (exact mod 2^32 in any order), after ks_init_kernel has written (0, b').
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -73,6 +81,7 @@ struct __align__(16) KsSmem {
 struct KsProducer {
     const uint32_t *T;
     uint32_t total, issued, chunk_words;
+    uint32_t base, per_batch;   // first (i, jp) chunk of this CTA's slice, chunks per batch
 };
 
 __device__ __forceinline__ void ks_produce(KsSmem &sm, KsProducer &pr, uint32_t upto)
@@ -86,7 +95,7 @@ __device__ __forceinline__ void ks_produce(KsSmem &sm, KsProducer &pr, uint32_t 
                 return;
             }
         }
-        const uint32_t chunk = q % (RING_N * KS_PAIRS);   // (i, jp) of this chunk
+        const uint32_t chunk = pr.base + q % pr.per_batch;   // (i, jp) of this chunk
         mbar_arrive_expect_tx(&sm.full_bar[s], pr.chunk_words * 4u);
         bulk_copy_g2s(sm.ring[s], pr.T + (size_t)chunk * pr.chunk_words, pr.chunk_words * 4u, &sm.full_bar[s]);
         pr.issued++;
@@ -104,7 +113,13 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
     const int V = n + 1;
     const uint32_t chunk_words = (uint32_t)(KS_CROWS * W);
     const size_t nbatches = (njobs + KS_CT - 1) / KS_CT;
-    const uint32_t per_batch = RING_N * KS_PAIRS;
+    // Input-coefficient slice of this CTA (the whole range unless grid.y > 1), in blocks of
+    // KS_ICH coefficients.
+    const bool sliced = gridDim.y > 1;
+    const int nblk = RING_N / KS_ICH;
+    const int i_begin = (int)(blockIdx.y * nblk / gridDim.y) * KS_ICH;
+    const int i_end = (int)((blockIdx.y + 1) * nblk / gridDim.y) * KS_ICH;
+    const uint32_t per_batch = (uint32_t)(i_end - i_begin) * KS_PAIRS;
 
     if (tid == 0) {
         for (int s = 0; s < KS_RING; s++) {
@@ -121,6 +136,8 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
     pr.T = T;
     pr.chunk_words = chunk_words;
     pr.issued = 0;
+    pr.base = (uint32_t)i_begin * KS_PAIRS;
+    pr.per_batch = per_batch;
     const size_t my_batches = blockIdx.x < nbatches ? (nbatches - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     pr.total = (uint32_t)(my_batches * per_batch);
     if (producer) ks_produce(sm, pr, KS_RING);
@@ -158,9 +175,10 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
 #pragma unroll
         for (int c = 0; c < KS_CPW; c++)
 #pragma unroll
-            for (int q = 0; q < KS_CPT; q++) acc[c][q] = (lane + 32 * q == n) ? sm.body[warp * KS_CPW + c] : 0u;
+            for (int q = 0; q < KS_CPT; q++)
+                acc[c][q] = (!sliced && lane + 32 * q == n) ? sm.body[warp * KS_CPW + c] : 0u;
 
-        for (int i0 = 0; i0 < RING_N; i0 += KS_ICH) {
+        for (int i0 = i_begin; i0 < i_end; i0 += KS_ICH) {
             if (__syncthreads_or(!ok)) {
                 ok = false;
                 break;
@@ -216,7 +234,9 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
 #pragma unroll
             for (int q = 0; q < KS_CPT; q++) {
                 const int col = lane + 32 * q;
-                if (col < V) out[(size_t)o * V + col] = acc[c][q];
+                if (col >= V) continue;
+                if (sliced) atomicAdd(&out[(size_t)o * V + col], acc[c][q]);
+                else out[(size_t)o * V + col] = acc[c][q];
             }
         }
         __syncthreads();
@@ -229,6 +249,33 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
         for (uint32_t q = firstq; q < pr.issued; q++)
             if (!mbar_wait_bounded(&sm.full_bar[q % KS_RING], (q / KS_RING) & 1u, &never))
                 atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+}
+
+// Sliced key switch: every output row starts as (0, b') (b' of its summed inputs plus bconst).
+__global__ void ks_init_kernel(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, int n)
+{
+    const int V = n + 1;
+    const size_t total = njobs * (size_t)V;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t g = idx / V;
+        const int w = (int)(idx % V);
+        int e1, e2 = -1, o;
+        uint32_t bc = 0u;
+        if (jobs) {
+            const KsJob J = jobs[g];
+            e1 = J.e1; e2 = J.e2; bc = J.bconst; o = J.out;
+        } else {
+            e1 = (int)g; o = (int)g;
+            if (dense_mux) { e2 = (int)(g + njobs); bc = T_EIGHTH; }
+        }
+        uint32_t v = 0u;
+        if (w == n) {
+            v = ext[(size_t)e1 * EXT_STRIDE + RING_N] + bc;
+            if (e2 >= 0) v += ext[(size_t)e2 * EXT_STRIDE + RING_N];
+        }
+        out[(size_t)o * V + w] = v;
     }
 }
 
@@ -246,6 +293,16 @@ cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int 
     cudaError_t e = cudaFuncSetAttribute(ks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t nb = (njobs + KS_CT - 1) / KS_CT;
+    if (2 * nb < (size_t)num_sms) {
+        // Too few batches to fill the GPU: split the input coefficients (see above).
+        const int slices = (int)std::min<size_t>((size_t)(RING_N / KS_ICH), (size_t)num_sms / nb);
+        const size_t total = njobs * (size_t)(n + 1);
+        const int ig = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms * 8);
+        ks_init_kernel<<<ig, 256, 0, st>>>(ext, jobs, njobs, dense_mux, out, n);
+        ks_kernel<<<dim3((unsigned)nb, (unsigned)slices), KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux, out, T,
+                                                                                  n, err);
+        return cudaGetLastError();
+    }
     const int grid = (int)(nb < (size_t)num_sms ? nb : (size_t)num_sms);
     ks_kernel<<<grid, KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux, out, T, n, err);
     return cudaGetLastError();
