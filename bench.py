@@ -147,6 +147,7 @@ def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int =
     ctx.lp_load_bsk_device(bsk)
     ctx.lp_load_ksk_device(ksk)
     del bsk, ksk
+    ctx.split_max = ctx.lp_autotune()   # split/batched blind-rotation crossing on this GPU
     A, B = synth.nand_pairs(seed_inputs, count)
     cts = []
     for bits, off in ((A, 0), (B, count)):
@@ -429,6 +430,7 @@ def _keys_for(n: int):
     ctx = locpir.Context(0, p)
     ctx.lp_load_bsk_device(bsk)
     ctx.lp_load_ksk_device(ksk)
+    ctx.split_max = ctx.lp_autotune()
     return ctx, p, s_dev
 
 
@@ -745,6 +747,7 @@ def run_gpu(args) -> None:
         "batched_speedup_vs_per_gate": (value / world / per_gate) if per_gate else None,
         "decrypt_errors": wrong,
         "locpir": loc,
+        "autotune": {"split_max": ctx.split_max},
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

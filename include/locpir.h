@@ -236,6 +236,15 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
 #define LP_KS_TENSOR_INT8 1
 int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
 
+/* lp_autotune: times both NTT blind-rotation kernels on this device (synthetic inputs, levels
+ * of 1-4 ciphertexts per SM, CUDA events, about 0.2 s) and sets the widest level the default
+ * engine runs split: the largest multiple of the SM count up to which the split kernel is
+ * still faster (never below one per SM).  Without it the rule is two ciphertexts per SM,
+ * measured on GB300.  *split_max_out (may be NULL) receives the chosen width.  Needs both keys
+ * (LP_ENOKEY); uses the context's scratch, so call it while no other work of this context is
+ * in flight (not while a server runs).  Results of later calls are bit-identical either way. */
+int lp_autotune(lp_ctx *ctx, int *split_max_out);
+
 /* Plans: lp_plan_locpir schedules a batch of queries once (levels, job records, a plan-owned
  * pool and scratch) and captures the whole evaluation -- input copies from the queries' pointers,
  * every level's pre-combination / blind-rotation / key-switch pass, output copies -- into one

@@ -584,14 +584,16 @@ cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, con
 
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
-                      cudaStream_t st, int variant)
+                      cudaStream_t st, int variant, int split_max)
 {
     if (jobs <= 0) return cudaSuccess;
     BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
     // Policy (measured on GB300): a split CTA finishes one ciphertext in 4.4-4.8 ms, a batched
     // wave of up to 4 per SM takes 13.3-14.3 ms, so levels of up to two ciphertexts per SM run
-    // split (one or two split waves) and larger ones batched.
-    const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= 2 * num_sms);
+    // split (one or two split waves) and larger ones batched, unless lp_autotune measured
+    // another crossing on this device.
+    const int smax = split_max > 0 ? split_max : 2 * num_sms;
+    const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= smax);
     if (split) {
         const size_t smem = sizeof(SplitSmem);
         cudaError_t e = cudaFuncSetAttribute(br_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

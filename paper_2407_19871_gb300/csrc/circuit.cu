@@ -146,7 +146,8 @@ static int enqueue_schedule(lp_ctx *c, const Schedule &S, const RunBufs &B, cuda
         cudaEvent_t ev0 = nullptr;
         if (timed) timer_begin(c, "br", st, &ev0);
         e = launch_br(B.abar, abar_stride(c), B.ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
-                      static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)ps.br_cnt, T_EIGHTH, err, c->num_sms, st);
+                      static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)ps.br_cnt, T_EIGHTH, err, c->num_sms, st,
+                      BR_VARIANT_AUTO, c->br_split_max);
         if (timed) timer_end(c, "br", st, ev0);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");

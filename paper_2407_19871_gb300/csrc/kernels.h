@@ -24,15 +24,17 @@ struct KsJob {
 
 size_t br_smem_bytes();
 size_t br_split_smem_bytes();
-// Blind-rotation kernel choice: AUTO runs levels of at most two ciphertexts per SM split
+// Blind-rotation kernel choice: AUTO runs levels of at most split_max ciphertexts split
 // (br_split_kernel, one ciphertext per CTA over 12 warps) and larger ones batched
-// (br_kernel, BR_SLOTS ciphertexts per CTA); the other two force one kernel.
+// (br_kernel, BR_SLOTS ciphertexts per CTA); split_max <= 0 means the measured GB300 rule,
+// two ciphertexts per SM (lp_autotune measures it on the device at hand).  The other two
+// variants force one kernel.
 constexpr int BR_VARIANT_AUTO = 0;
 constexpr int BR_VARIANT_BATCHED = 1;
 constexpr int BR_VARIANT_SPLIT = 2;
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms, cudaStream_t st,
-                      int variant = BR_VARIANT_AUTO);
+                      int variant = BR_VARIANT_AUTO, int split_max = 0);
 cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane, uint32_t scale0,
                               uint32_t scale1, int num_sms, cudaStream_t st);
 cudaError_t launch_precomb_dense(int op, const uint32_t *a, const uint32_t *b, const uint32_t *c, int n,

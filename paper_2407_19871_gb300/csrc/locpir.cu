@@ -420,7 +420,7 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
     cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
-                              static_cast<int *>(c->err.ptr), c->num_sms, st, variant);
+                              static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max);
     timer_end(c, "br", st, ev0);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
@@ -461,6 +461,55 @@ extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
     }
     c->br_engine = br_engine;
     c->ks_engine = ks_engine;
+    return LP_OK;
+}
+
+extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (!c->have_bsk || !c->have_ksk) return fail(LP_ENOKEY, "load the bootstrapping and key-switching keys first");
+    cudaSetDevice(c->device);
+    const int S = c->num_sms, maxw = 4 * S, stride = abar_stride(c);
+    int rc = ensure_scratch(c, (size_t)maxw);
+    if (rc) return rc;
+    // Synthetic mod-switched inputs: every coefficient in [0, 2N) from a fixed LCG, so that no
+    // CMux step is skipped.
+    std::vector<uint16_t> h((size_t)maxw * stride);
+    uint32_t x = 12345u;
+    for (uint16_t &v : h) {
+        x = x * 1664525u + 1013904223u;
+        v = (uint16_t)(x >> 21);
+    }
+    cudaError_t e = cudaMemcpy(c->abar.ptr, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune inputs");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t[5][2] = {};
+    for (int k = 1; k <= 4 && e == cudaSuccess; k++) {
+        for (int v = 0; v < 2 && e == cudaSuccess; v++) {
+            const int variant = v ? BR_VARIANT_SPLIT : BR_VARIANT_BATCHED;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // warm-up, then timed
+                cudaEventRecord(e0, 0);
+                e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), stride, static_cast<uint32_t *>(c->ext.ptr),
+                              static_cast<const uint32_t *>(c->bsk_hat.ptr), static_cast<const uint2 *>(c->tw_lane.ptr),
+                              c->params.n, k * S, T_EIGHTH, static_cast<int *>(c->err.ptr), S, 0, variant);
+                c->launches++;
+                cudaEventRecord(e1, 0);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) cudaEventElapsedTime(&t[k][v], e0, e1);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if ((rc = ctx_check_err(c))) return rc;
+    // Levels below one wave always favour the split kernel; widen while it stays faster.
+    int best = S;
+    for (int k = 2; k <= 4 && t[k][1] < t[k][0]; k++) best = k * S;
+    c->br_split_max = best;
+    if (split_max_out) *split_max_out = best;
     return LP_OK;
 }
 

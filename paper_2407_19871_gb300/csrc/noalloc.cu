@@ -91,7 +91,7 @@ extern "C" int lp_gate_batch_noalloc(lp_ctx *c, int op, const uint32_t *a, const
     if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
     e = launch_br(abar, abar_stride(c), ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
                   static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)(count * halves), T_EIGHTH,
-                  static_cast<int *>(c->err.ptr), c->num_sms, st);
+                  static_cast<int *>(c->err.ptr), c->num_sms, st, BR_VARIANT_AUTO, c->br_split_max);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
     e = launch_ks(ext, nullptr, count, op == LP_MUX, out, static_cast<const uint32_t *>(c->ksk.ptr), n,

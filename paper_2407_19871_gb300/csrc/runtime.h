@@ -42,6 +42,7 @@ struct lp_ctx {
     lp::Server *server = nullptr;   // query server (lp_server_start), if running
     // Alternative tensor-core engines (tensor_engine.cu) and their state.
     int br_engine = LP_BR_NTT, ks_engine = LP_KS_TABLE;
+    int br_split_max = 0;           // widest level run split (0: the default rule; lp_autotune)
     void *blas = nullptr;           // cuBLAS handle, created on first use
     lp::DevBuf bsk_coef;            // coefficient-domain BSK (Toeplitz engine)
     lp::DevBuf tc_T, tc_D, tc_C, tc_acc, ks_A, ks_H, ks_C, ks_aux;

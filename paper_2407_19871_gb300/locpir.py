@@ -32,7 +32,7 @@ EXPORTS = [
     "lp_preprocess_services", "lp_selftest_wait_timeout",
     "lp_server_start", "lp_server_submit", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
-    "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines",
+    "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
 ]
 LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_uint64)]),
             "lp_plan_destroy": (i, [vp]),
             "lp_set_engines": (i, [vp, i, i]),
+            "lp_autotune": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -349,6 +350,13 @@ class Context:
     # ---- alternative product engines
     def lp_set_engines(self, br_engine: int = LP_BR_NTT, ks_engine: int = LP_KS_TABLE) -> None:
         _check(lib().lp_set_engines(self.h, br_engine, ks_engine), "lp_set_engines")
+
+    def lp_autotune(self) -> int:
+        """Measure the split/batched blind-rotation crossing on this GPU; returns the widest
+        level (ciphertexts) the default engine now runs split."""
+        v = ctypes.c_int()
+        _check(lib().lp_autotune(self.h, ctypes.byref(v)), "lp_autotune")
+        return v.value
 
     # ---- server-known bounds (beyond the paper)
     def lp_compare_known_batch(self, kind: int, is_signed: int, l: int, x, k, out, count: int, stream=None) -> None:

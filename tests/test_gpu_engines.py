@@ -119,3 +119,20 @@ def test_split_kernel_beyond_one_wave(engines_ctx, keys):
     assert_same(outs[4], outs[3], "split vs batched")
     rows = [0, count // 2, count - 1]
     assert_same(outs[4][rows], oracle.bootstrap_extract(keys, lwe[rows]), "split vs oracle (sampled rows)")
+
+
+def test_autotune_sets_a_crossing_and_keeps_bits(gpu_ctx, keys):
+    """lp_autotune picks a multiple of the SM count in [1, 4] per SM; a gate batch afterwards
+    is still bit-identical to the oracle."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = gpu_ctx.lp_autotune()
+    assert w % sms == 0 and sms <= w <= 4 * sms
+    p = keys.params
+    bits = synth.bits(13, 1, 10).reshape(2, 5)
+    a = oracle.encrypt(keys.s, bits[0], synth.lwe_draws(13, 5))
+    b = oracle.encrypt(keys.s, bits[1], synth.lwe_draws(13, 5, offset=5))
+    out = empty_dev(5, p.n + 1)
+    gpu_ctx.lp_gate_batch(oracle.AND, to_dev(a), to_dev(b), None, out, 5)
+    gpu_ctx.lp_sync()
+    assert_same(to_host(out), oracle.gate_batch(keys, oracle.AND, a, b, None), "after autotune")
