@@ -283,6 +283,9 @@ typedef struct lp_stats {
 } lp_stats;
 int lp_server_start(lp_ctx *ctx, size_t mem_budget, int policy);
 int lp_server_submit(lp_ctx *ctx, const lp_query *q, uint64_t *ticket);
+/* The same for a query with server-known bounds (lp_query_known; its bounds array is copied
+ * during the call, the device pointers must stay valid until the result is written). */
+int lp_server_submit_known(lp_ctx *ctx, const lp_query_known *q, uint64_t *ticket);
 int lp_server_poll(lp_ctx *ctx, uint64_t ticket, int *done);
 int lp_server_wait(lp_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
 int lp_server_stats(lp_ctx *ctx, lp_stats *out);

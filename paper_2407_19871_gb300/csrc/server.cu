@@ -32,7 +32,9 @@ using Clock = std::chrono::steady_clock;
 
 struct SrvQuery {
     uint64_t ticket = 0;
-    lp_query q{};
+    lp_query q{};                   // for known bounds, q.boxes is unused
+    bool known = false;             // server-known (plaintext) bounds
+    std::vector<uint64_t> bounds;   // [n_boxes][4] when known
     Circuit C;
     std::vector<std::vector<int>> levels;
     std::vector<Sig> outs;
@@ -100,10 +102,14 @@ static void build_query(lp_ctx *c, SrvQuery &Q)
     const lp_query &q = Q.q;
     Q.inputs[0] = Q.C.inputs(q.l);
     Q.inputs[1] = Q.C.inputs(q.l);
-    Q.inputs[2] = Q.C.inputs(4 * q.l * q.n_boxes);
+    Q.inputs[2] = Q.C.inputs(Q.known ? 0 : 4 * q.l * q.n_boxes);
     Q.inputs[3] = Q.C.inputs(q.m * q.n_boxes);
-    Q.outs = build_locpir(Q.C, q.l, q.is_signed != 0, Q.inputs[0], Q.inputs[1], q.n_boxes, Q.inputs[2], q.m,
-                          Q.inputs[3], q.comb);
+    if (Q.known)
+        Q.outs = build_locpir_known(Q.C, q.l, q.is_signed != 0, Q.inputs[0], Q.inputs[1], q.n_boxes, Q.bounds.data(),
+                                    q.m, Q.inputs[3], q.comb);
+    else
+        Q.outs = build_locpir(Q.C, q.l, q.is_signed != 0, Q.inputs[0], Q.inputs[1], q.n_boxes, Q.inputs[2], q.m,
+                              Q.inputs[3], q.comb);
     Q.levels = levels_of(Q.C);
     Q.nwires = Q.C.depth.size();
     (void)c;
@@ -117,8 +123,10 @@ static int admit(Server &S, SrvQuery &Q)
     uint32_t *pool = static_cast<uint32_t *>(S.pool.ptr) + Q.pool_off;
     const lp_query &q = Q.q;
     const uint32_t *srcs[4] = {q.x, q.y, q.boxes, q.services};
-    const size_t cnts[4] = {(size_t)q.l, (size_t)q.l, (size_t)4 * q.l * q.n_boxes, (size_t)q.m * q.n_boxes};
+    const size_t cnts[4] = {(size_t)q.l, (size_t)q.l, Q.known ? 0 : (size_t)4 * q.l * q.n_boxes,
+                            (size_t)q.m * q.n_boxes};
     for (int k = 0; k < 4; k++) {
+        if (!cnts[k]) continue;
         cudaError_t e = cudaMemcpyAsync(pool + (size_t)Q.inputs[k] * W, srcs[k], cnts[k] * W * 4,
                                         cudaMemcpyDeviceToDevice, S.st);
         if (e != cudaSuccess) return cuda_fail(e, "server: copy query inputs");
@@ -311,15 +319,10 @@ extern "C" int lp_server_start(lp_ctx *c, size_t mem_budget, int policy)
     return LP_OK;
 }
 
-extern "C" int lp_server_submit(lp_ctx *c, const lp_query *q, uint64_t *ticket)
+// Queue a built query (FIFO) or reject it against the budget; takes ownership of Q.
+static int submit_query(lp_ctx *c, SrvQuery *Q, uint64_t *ticket)
 {
-    if (!c || !q || !ticket) return fail(LP_EINVAL, "null argument");
     Server *S = c->server;
-    if (!S) return fail(LP_EINVAL, "no server running on this context");
-    int rc = check_query(*q);
-    if (rc) return rc;
-    SrvQuery *Q = new SrvQuery();
-    Q->q = *q;
     build_query(c, *Q);
     const size_t need = query_words(c, Q->nwires);
     std::lock_guard<std::mutex> lock(S->mu);
@@ -350,6 +353,33 @@ extern "C" int lp_server_submit(lp_ctx *c, const lp_query *q, uint64_t *ticket)
     *ticket = Q->ticket;
     S->cv.notify_all();
     return LP_OK;
+}
+
+extern "C" int lp_server_submit(lp_ctx *c, const lp_query *q, uint64_t *ticket)
+{
+    if (!c || !q || !ticket) return fail(LP_EINVAL, "null argument");
+    if (!c->server) return fail(LP_EINVAL, "no server running on this context");
+    int rc = check_query(*q);
+    if (rc) return rc;
+    SrvQuery *Q = new SrvQuery();
+    Q->q = *q;
+    return submit_query(c, Q, ticket);
+}
+
+extern "C" int lp_server_submit_known(lp_ctx *c, const lp_query_known *q, uint64_t *ticket)
+{
+    if (!c || !q || !ticket) return fail(LP_EINVAL, "null argument");
+    if (!c->server) return fail(LP_EINVAL, "no server running on this context");
+    lp_query chk{q->l, q->is_signed, q->n_boxes, q->m, q->comb, q->x, q->y,
+                 reinterpret_cast<const uint32_t *>(q->bounds), q->services, q->out_service};
+    int rc = check_query(chk);
+    if (rc) return rc;
+    SrvQuery *Q = new SrvQuery();
+    Q->q = chk;
+    Q->q.boxes = nullptr;
+    Q->known = true;
+    Q->bounds.assign(q->bounds, q->bounds + 4 * (size_t)q->n_boxes);   // the caller's array may go away
+    return submit_query(c, Q, ticket);
 }
 
 extern "C" int lp_server_poll(lp_ctx *c, uint64_t ticket, int *done)

@@ -30,7 +30,7 @@ EXPORTS = [
     "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
     "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
     "lp_preprocess_services", "lp_selftest_wait_timeout",
-    "lp_server_start", "lp_server_submit", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
+    "lp_server_start", "lp_server_submit", "lp_server_submit_known", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
 ]
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "lp_selftest_wait_timeout": (i, [vp, u32, vp]),
             "lp_server_start": (i, [vp, sz, i]),
             "lp_server_submit": (i, [vp, ctypes.POINTER(lp_query), ctypes.POINTER(ctypes.c_uint64)]),
+            "lp_server_submit_known": (i, [vp, ctypes.POINTER(lp_query_known), ctypes.POINTER(ctypes.c_uint64)]),
             "lp_server_poll": (i, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
             "lp_server_wait": (i, [vp, ctypes.c_uint64, u32]),
             "lp_server_stats": (i, [vp, ctypes.POINTER(lp_stats)]),
@@ -369,22 +370,26 @@ class Context:
                                             kb.ctypes.data, _dptr(out, count * W, "out"), count, _stream(stream)),
                "lp_compare_known_batch")
 
+    def _query_known_struct(self, q: dict):
+        """(lp_query_known, bounds array to keep alive) for a known-bounds query dict."""
+        W = self.n + 1
+        l, nb, m = q["l"], q["n_boxes"], q["m"]
+        b = np.ascontiguousarray(np.asarray(q["bounds"], dtype=np.uint64).reshape(-1))
+        if b.size < 4 * nb:
+            raise ValueError(f"bounds has {b.size} values, the query reads {4 * nb}")
+        return lp_query_known(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
+                              _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"), b.ctypes.data,
+                              _dptr(q["services"], nb * m * W, "services"),
+                              _dptr(q["out_service"], m * W, "out_service")), b
+
     def lp_locpir_known_batch(self, queries: list[dict], stream=None) -> None:
         """queries: dicts with l, is_signed, n_boxes, m, comb, bounds ([n_boxes][4] ints
         X1, X2, Y1, Y2) and tensors x, y, services, out_service."""
-        W = self.n + 1
         arr = (lp_query_known * len(queries))()
         keep = []
         for i, q in enumerate(queries):
-            l, nb, m = q["l"], q["n_boxes"], q["m"]
-            b = np.ascontiguousarray(np.asarray(q["bounds"], dtype=np.uint64).reshape(-1))
-            if b.size < 4 * nb:
-                raise ValueError(f"bounds has {b.size} values, the query reads {4 * nb}")
+            arr[i], b = self._query_known_struct(q)
             keep.append(b)
-            arr[i] = lp_query_known(l, q.get("is_signed", 0), nb, m, q.get("comb", LP_XOR_TREE),
-                                    _dptr(q["x"], l * W, "x"), _dptr(q["y"], l * W, "y"), b.ctypes.data,
-                                    _dptr(q["services"], nb * m * W, "services"),
-                                    _dptr(q["out_service"], m * W, "out_service"))
         _check(lib().lp_locpir_known_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_known_batch")
 
     # ---- plans (CUDA graphs)
@@ -407,6 +412,15 @@ class Context:
         t = ctypes.c_uint64()
         qs = self._query_struct(q)
         _check(lib().lp_server_submit(self.h, ctypes.byref(qs), ctypes.byref(t)), "lp_server_submit")
+        self._server_refs[t.value] = q
+        return t.value
+
+    def lp_server_submit_known(self, q: dict) -> int:
+        """Submit a known-bounds query dict (as in lp_locpir_known_batch); its bounds are copied
+        by the call, its tensors are kept referenced until lp_server_stop."""
+        t = ctypes.c_uint64()
+        qs, _ = self._query_known_struct(q)
+        _check(lib().lp_server_submit_known(self.h, ctypes.byref(qs), ctypes.byref(t)), "lp_server_submit_known")
         self._server_refs[t.value] = q
         return t.value
 

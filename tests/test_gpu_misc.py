@@ -70,6 +70,35 @@ def test_lambda80_dimension_matches_oracle():
         ctx.close()
 
 
+@pytest.mark.parametrize("n", [1, 7, 639])
+def test_lwe_dimension_edges_match_oracle(n):
+    """The smallest, an odd and the largest supported LWE dimension (n + 1 = 640 words fills
+    the key switch's 20 words per lane exactly), on both blind-rotation kernels."""
+    from paper_2407_19871_gb300 import locpir
+    p = synth.Params(n=n)
+    kn = oracle.keygen(synth.key_draws(6, p))
+    lp = locpir.params_default()
+    lp.n = n
+    ctx = locpir.Context(0, lp)
+    try:
+        ctx.lp_load_bsk(np.ascontiguousarray(kn.bsk.reshape(-1)))
+        ctx.lp_load_ksk(np.ascontiguousarray(kn.ksk.reshape(-1)))
+        cnt = 5
+        A, B, Cb = (synth.bits(85, k, cnt) for k in (1, 2, 3))
+        a, b, c = (oracle.encrypt(kn.s, X, synth.lwe_draws(85, cnt, p, offset=k * cnt))
+                   for k, X in enumerate((A, B, Cb)))
+        for op in (oracle.AND, oracle.MUX):
+            want = oracle.gate_batch(kn, op, a, b, c if op == oracle.MUX else None)
+            for variant in (locpir.LP_BR_NTT_BATCHED, locpir.LP_BR_NTT_SPLIT):
+                ctx.lp_set_engines(variant, 0)
+                out = empty_dev(cnt, p.n + 1)
+                ctx.lp_gate_batch(op, to_dev(a), to_dev(b), to_dev(c) if op == oracle.MUX else None, out, cnt)
+                ctx.lp_sync()
+                assert_same(to_host(out), want, f"n={n} op={op} variant={variant}")
+    finally:
+        ctx.close()
+
+
 def _mkquery(keys, seed, l, boxes, services, px, py, comb=0):
     n = keys.params.n
     bits = lambda v: synth.int_to_bits(v, l)

@@ -111,3 +111,46 @@ def test_server_budget_refusals(gpu_ctx, keys):
         assert st["rejected"] == 2 and st["completed"] == 1
     finally:
         gpu_ctx.lp_server_stop()
+
+
+def test_server_mixes_known_and_encrypted_bounds(gpu_ctx, keys):
+    """Known-bounds queries (lp_server_submit_known) and encrypted-bounds queries share the
+    server's ticks; each known-bounds result equals lp_locpir_known_batch on the same query
+    alone, bit for bit, and each encrypted one equals lp_locpir_query alone."""
+    n = keys.params.n
+    enc = [_query(keys, 950 + k, l, boxes, svc, px, py) for k, (l, boxes, svc, px, py) in enumerate(SPECS[:3])]
+    known = []
+    for k, (l, boxes, svc, px, py) in enumerate(SPECS[1:]):
+        q = _query(keys, 970 + k, l, boxes, svc, px, py, comb=k % 3)
+        known.append(dict(l=q["l"], is_signed=0, n_boxes=q["n_boxes"], m=q["m"], comb=q["comb"], x=q["x"], y=q["y"],
+                          bounds=boxes, services=q["services"], out_service=empty_dev(q["m"], n + 1)))
+    alone_enc = []
+    for q in enc:
+        out = empty_dev(q["m"], n + 1)
+        gpu_ctx.lp_locpir_query(q["l"], 0, q["x"], q["y"], q["n_boxes"], q["boxes"], q["m"], q["services"],
+                                q["comb"], out)
+        alone_enc.append(out)
+    alone_known = []
+    for q in known:
+        qa = dict(q, out_service=empty_dev(q["m"], n + 1))
+        gpu_ctx.lp_locpir_known_batch([qa])
+        alone_known.append(qa["out_service"])
+    gpu_ctx.lp_sync()
+    gpu_ctx.lp_server_start(1 << 30)
+    try:
+        tickets = []
+        for k in range(max(len(enc), len(known))):
+            if k < len(known):
+                tickets.append(gpu_ctx.lp_server_submit_known(known[k]))
+            if k < len(enc):
+                tickets.append(gpu_ctx.lp_server_submit(enc[k]))
+        for t in tickets:
+            gpu_ctx.lp_server_wait(t, 300000)
+    finally:
+        gpu_ctx.lp_server_stop()
+    for k, (q, a) in enumerate(zip(known, alone_known)):
+        assert_same(to_host(q["out_service"]), to_host(a), f"known-bounds query {k} in the mix vs alone")
+    for k, (q, a) in enumerate(zip(enc, alone_enc)):
+        assert_same(to_host(q["out_service"]), to_host(a), f"encrypted-bounds query {k} in the mix vs alone")
+    # spec 1's point (45, 20) lies in its second box only
+    assert oracle.decrypt(keys.s, to_host(known[0]["out_service"])).tolist() == [0, 1, 1]
