@@ -51,9 +51,11 @@ _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 
 def lib() -> ctypes.CDLL:
+    """The oracle library.  ORACLE_LIB, when set, names a prebuilt copy to load instead; the
+    mutation tests use it to run the pins against deliberately broken builds."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
         c_int, c_size, c_u32 = ctypes.c_int, ctypes.c_size_t, ctypes.c_uint32
         sig = {
             "or_poly_mul_schoolbook": (None, [c_int, _u32p, _u32p, _u32p]),
