@@ -450,6 +450,39 @@ def _timed(fn, reps: int = 3) -> float:
     return float(np.median(ts))
 
 
+def _random_query_time(ctx, p, s_dev, l: int, nb: int, m: int, seed: int) -> tuple[float, int]:
+    """One unsigned LocPIR query (XOR tree) with nb random boxes of l-bit bounds, a random point
+    and m-bit services: median seconds of lp_locpir_query (after a warm-up run) and the number
+    of service bits that decrypt wrongly against the plaintext truth."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    L = 1 << l
+    d = synth.splitmix64(4, seed, 4 * nb + 2)
+    boxes = []
+    for b in range(nb):
+        x1, x2 = sorted(int(v) % L for v in d[4 * b:4 * b + 2])
+        y1, y2 = sorted(int(v) % L for v in d[4 * b + 2:4 * b + 4])
+        boxes.append((x1, x2, y1, y2))
+    px, py = int(d[4 * nb]) % L, int(d[4 * nb + 1]) % L
+    svc = synth.bits(4, seed, nb * m).reshape(nb, m)
+    bits = np.concatenate([synth.int_to_bits(px, l), synth.int_to_bits(py, l)] +
+                          [synth.int_to_bits(v, l) for b in boxes for v in b] + [svc.reshape(-1)])
+    ct = _encrypt_bits(p, s_dev, bits, seed + 1)
+    W = p.n + 1
+    out = torch.empty(m, W, dtype=torch.int32, device="cuda")
+    run = lambda: ctx.lp_locpir_query(l, 0, ct[:l], ct[l:2 * l], nb, ct[2 * l:2 * l + 4 * l * nb], m,
+                                      ct[2 * l + 4 * l * nb:], locpir.LP_XOR_TREE, out)
+    sec = _timed(run)
+    want = np.zeros(m, np.uint8)
+    for (x1, x2, y1, y2), sv in zip(boxes, svc):
+        if x1 <= px < x2 and y1 <= py < y2:
+            want ^= sv
+    ph = torch.empty(m, dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, m)
+    wrong = int(((ph.cpu().numpy() > 0).astype(np.uint8) != want).sum())
+    return sec, wrong
+
+
 def paper_shapes() -> None:
     import torch
     from paper_2407_19871_gb300 import locpir
@@ -505,25 +538,21 @@ def paper_shapes() -> None:
                                                       (630, 16): 5.67}[(n, l)],
                               "paper_hardware": "Ryzen 5 3500X, TFHE library v1.1 (Table 2)"}), flush=True)
         if n == 630:
-            # Fig. 4(a): B_x = 10, m = 9, l in {8, 16, 24, 32}; unsigned random boxes.
-            for l in (8, 16, 24, 32):
-                rng = synth.splitmix64(4, 77 + l, 64)
-                bb = []
-                for b in range(10):
-                    a, c = sorted(int(v) % (1 << l) for v in rng[4 * b:4 * b + 2])
-                    d, e = sorted(int(v) % (1 << l) for v in rng[4 * b + 2:4 * b + 4])
-                    bb.append((a, c + 1, d, e + 1))
-                bits = np.concatenate([synth.int_to_bits(int(rng[60]) % (1 << l), l),
-                                       synth.int_to_bits(int(rng[61]) % (1 << l), l)] +
-                                      [synth.int_to_bits(v % (1 << l), l) for b in bb for v in b] +
-                                      [synth.bits(4, 500 + b, m) for b in range(10)])
-                ct = _encrypt_bits(p, s_dev, bits, 8)
-                out = torch.empty(m, W, dtype=torch.int32, device="cuda")
-                run = lambda: ctx.lp_locpir_query(l, 0, ct[:l], ct[l:2 * l], 10, ct[2 * l:42 * l], m, ct[42 * l:],
-                                                  locpir.LP_XOR_TREE, out)
-                print(json.dumps({"experiment": "fig4a", "l": l, "boxes": 10, "m": m, "seconds": _timed(run),
-                                  "paper_seconds": {8: 3.256, 16: 6.139, 24: 8.764, 32: 11.670}[l],
-                                  "paper_hardware": "Ryzen 5 3500X, 6 threads (Section 6.2)"}), flush=True)
+            # Fig. 4(a): time against (B_x, l) at m = 9; the paper prints its B_x = 10 row.
+            paper4a = {8: 3.256, 16: 6.139, 24: 8.764, 32: 11.670}
+            for nb in (2, 4, 6, 8, 10, 16, 28):
+                for l in (8, 16, 24, 32):
+                    sec, wrong = _random_query_time(ctx, p, s_dev, l, nb, m, seed=100 * nb + l)
+                    line = {"experiment": "fig4a", "l": l, "boxes": nb, "m": m, "seconds": sec, "wrong_bits": wrong}
+                    if nb == 10:
+                        line.update(paper_seconds=paper4a[l], paper_hardware="Ryzen 5 3500X, 6 threads (Section 6.2)")
+                    print(json.dumps(line), flush=True)
+            # Fig. 4(b): time against (m, B_x) at l = 16.
+            for nb in (2, 10, 28):
+                for mm in (9, 32, 64, 128):
+                    sec, wrong = _random_query_time(ctx, p, s_dev, 16, nb, mm, seed=7000 + 100 * nb + mm)
+                    print(json.dumps({"experiment": "fig4b", "l": 16, "boxes": nb, "m": mm, "seconds": sec,
+                                      "wrong_bits": wrong}), flush=True)
             # Server-known bounds (beyond the paper) against encrypted bounds, same city batch.
             for nq in (152, 608):
                 print(json.dumps(known_bounds_throughput(ctx, p, s_dev, nq)), flush=True)
