@@ -596,22 +596,27 @@ def serve(args) -> None:
                 e ^= sv
         expect.append(e)
     torch.cuda.synchronize()
-    ctx.lp_server_start(int(args.serve_budget_gb * 2**30))
+    policy = locpir.LP_SERVER_REJECT if args.serve_policy == "reject" else locpir.LP_SERVER_QUEUE
+    ctx.lp_server_start(int(args.serve_budget_gb * 2**30), policy)
     tickets, t0 = [], time.perf_counter()
     next_t = t0
+    offered, submit_s = 0, 0.0
     try:
         while True:
             now = time.perf_counter()
             if now - t0 >= args.serve_seconds:
                 break
             if now >= next_t:
-                k = len(tickets) % len(queries)
+                k = offered % len(queries)
+                offered += 1
                 q = dict(queries[k])
                 q["out_service"] = torch.empty(q["m"], W, dtype=torch.int32, device="cuda")
+                ts = time.perf_counter()
                 try:
                     tickets.append((ctx.lp_server_submit(q), k, q["out_service"]))
                 except locpir.LocpirError:
                     pass
+                submit_s += time.perf_counter() - ts
                 next_t += rng.exponential(1.0 / args.serve_rate)
             else:
                 time.sleep(min(next_t - now, 0.01))
@@ -628,6 +633,8 @@ def serve(args) -> None:
         locpir.lp_client_lwe_phase(p.n, s_dev, o, ph, o.shape[0])
         wrong += int(((ph.cpu().numpy() > 0).astype(np.uint8) != expect[k]).sum())
     print(json.dumps({"experiment": "serving", "shape": args.serve_shape, "arrival_rate_per_s": args.serve_rate,
+                      "policy": args.serve_policy, "offered": offered,
+                      "submit_ms_mean": 1e3 * submit_s / max(offered, 1),
                       "arrival_seconds": args.serve_seconds, "drain_seconds": args.serve_drain,
                       "memory_budget_gb": args.serve_budget_gb, "distinct_queries": len(queries),
                       "submitted": st["submitted"], "admitted": st["admitted"], "completed": st["completed"],
@@ -811,6 +818,7 @@ def main():
     ap.add_argument("--serve-drain", type=float, default=30.0)
     ap.add_argument("--serve-budget-gb", type=float, default=4.0)
     ap.add_argument("--serve-distinct", type=int, default=4)
+    ap.add_argument("--serve-policy", default="queue", choices=["queue", "reject"])
     ap.add_argument("--count", type=int, default=COUNT,
                     help="gates per step (default 65,536; smaller values are for profiling only)")
     args = ap.parse_args()

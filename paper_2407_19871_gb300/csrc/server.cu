@@ -96,6 +96,15 @@ static void pool_free(Server &S, size_t off, size_t words)
     S.free_list.swap(merged);
 }
 
+// Release the host-side circuit of a query (a waiting query keeps only its arguments, so that
+// a long queue costs little host memory; admission builds the circuit again).
+static void drop_circuit(SrvQuery &Q)
+{
+    Q.C = Circuit();
+    std::vector<std::vector<int>>().swap(Q.levels);
+    std::vector<Sig>().swap(Q.outs);
+}
+
 // Build the circuit of one query (host only).
 static void build_query(lp_ctx *c, SrvQuery &Q)
 {
@@ -113,6 +122,17 @@ static void build_query(lp_ctx *c, SrvQuery &Q)
     Q.levels = levels_of(Q.C);
     Q.nwires = Q.C.depth.size();
     (void)c;
+}
+
+// Wires of an encrypted-bounds query's circuit without building it: the inputs
+// (2l + 4l B_x + m B_x), per box 4 comparators of l XNOR + l MUX, 3 validation ANDs and m
+// service ANDs, the combine (B_x m XORs as a chain, (B_x - 1) m as a tree), and the shared
+// constant wire.  build_locpir makes exactly these (checked again at admission).
+static size_t encrypted_query_wires(const lp_query &q)
+{
+    const size_t l = (size_t)q.l, nb = (size_t)q.n_boxes, m = (size_t)q.m;
+    const size_t combine = q.comb == LP_XOR_CHAIN ? nb * m : (nb - 1) * m;
+    return 2 * l + 4 * l * nb + m * nb + nb * (8 * l + 3 + m) + combine + 1;
 }
 
 // Admission: reserve pool space and copy the inputs in (server stream).
@@ -235,8 +255,7 @@ static int tick(Server &S)
         S.completed++;
         S.latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - Q->t_submit).count());
         pool_free(S, Q->pool_off, query_words(c, Q->nwires));
-        Q->C = Circuit();
-        Q->levels.clear();
+        drop_circuit(*Q);
     }
     S.active.erase(std::remove_if(S.active.begin(), S.active.end(), [](SrvQuery *Q) { return Q->done; }),
                    S.active.end());
@@ -258,7 +277,12 @@ static void server_loop(Server *Sp)
                 if (!pool_alloc(S, query_words(S.c, Q->nwires), &off)) break;
                 Q->pool_off = off;
                 S.waiting.pop_front();
-                int rc = admit(S, *Q);
+                const size_t reserved = Q->nwires;
+                if (Q->levels.empty()) build_query(S.c, *Q);   // not built, or dropped while it waited
+                int rc = Q->nwires == reserved
+                             ? admit(S, *Q)
+                             : fail(LP_ECUDA, "server: query circuit has %zu wires, %zu were reserved", Q->nwires,
+                                    reserved);
                 if (rc) {
                     S.error = rc;
                     S.stop = true;
@@ -323,7 +347,10 @@ extern "C" int lp_server_start(lp_ctx *c, size_t mem_budget, int policy)
 static int submit_query(lp_ctx *c, SrvQuery *Q, uint64_t *ticket)
 {
     Server *S = c->server;
-    build_query(c, *Q);
+    // Encrypted-bounds circuits have a closed-form size, so submitting one costs O(1); the
+    // size of a known-bounds circuit depends on the bound bits, so it is built here.
+    if (Q->known) build_query(c, *Q);
+    else Q->nwires = encrypted_query_wires(Q->q);
     const size_t need = query_words(c, Q->nwires);
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->stop) {
@@ -347,6 +374,8 @@ static int submit_query(lp_ctx *c, SrvQuery *Q, uint64_t *ticket)
     }
     Q->ticket = S->next_ticket++;
     Q->t_submit = Clock::now();
+    // Only its size was needed here; the circuit is built again at admission.
+    drop_circuit(*Q);
     S->all[Q->ticket] = Q;
     S->waiting.push_back(Q);
     S->submitted++;
