@@ -380,15 +380,28 @@ def cpu_baseline(seconds_target: float = 15.0) -> dict:
             "sample": f"first {S} of the 65,536 NAND gates (OpenMP over gates, {cores} threads), {dt:.1f} s"}
 
 
+def kernel_source_sha256(spec: list[str]) -> str:
+    """SHA-256 of the sources a kernel is built from.  An entry "path#marker" takes the file's
+    text before the first line that starts with marker (the kernel's part of a larger file)."""
+    import hashlib
+    h = hashlib.sha256()
+    for entry in spec:
+        path, _, marker = entry.partition("#")
+        text = open(os.path.join(ROOT, path), "rb").read()
+        if marker:
+            cut = text.find(("\n" + marker).encode())
+            text = text[:cut + 1] if cut >= 0 else text
+        h.update(text)
+    return h.hexdigest()
+
+
 def br_traffic():
     """DRAM bytes per blind-rotation launch from the recorded ncu capture, or None once the
     kernel sources differ from the ones the counters were taken on."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        h = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["source_files"]))
-        if h.hexdigest() != rec["br_kernel_source_sha256"]:
+        if kernel_source_sha256(rec["source_files"]) != rec["br_kernel_source_sha256"]:
             return None
         return rec["br_kernel_dram_bytes_per_launch"]
     except Exception:
