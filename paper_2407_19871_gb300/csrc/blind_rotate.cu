@@ -25,9 +25,12 @@
 // them with the key chunk, accumulating both output components in 64-bit registers
 // (key stored as NTT(b) N^-1 2^32 mod p, one Montgomery reduction per coefficient);
 // it inverse-transforms the 2 sums together (their butterflies interleaved).  The pair then
-// swaps half of its residues through
-// shared memory: the prime-0 warp recombines component 0 (centred CRT) and adds it to
-// ACC, the prime-1 warp component 1.
+// swaps half of its residues through shared memory: the prime-0 warp recombines component 0
+// (centred CRT) and adds it to ACC, the prime-1 warp component 1.
+//
+// The file also holds br_split_kernel, which spreads one ciphertext over 12 warps for levels
+// too small to fill the GPU (see its section), and launch_br, which picks one of the two per
+// level.
 #include "common.cuh"
 #include "kernels.h"
 #include "ntt.cuh"
