@@ -102,6 +102,8 @@ __device__ __forceinline__ void ks_produce(KsSmem &sm, KsProducer &pr, uint32_t 
     }
 }
 
+// Sliced: the grid.y slices of the input coefficients add into pre-initialised outputs.
+template <bool Sliced>
 __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, const KsJob *jobs, size_t njobs,
                                                            int dense_mux, uint32_t *out, const uint32_t *T, int n,
                                                            int *err)
@@ -115,10 +117,9 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
     const size_t nbatches = (njobs + KS_CT - 1) / KS_CT;
     // Input-coefficient slice of this CTA (the whole range unless grid.y > 1), in blocks of
     // KS_ICH coefficients.
-    const bool sliced = gridDim.y > 1;
     const int nblk = RING_N / KS_ICH;
-    const int i_begin = (int)(blockIdx.y * nblk / gridDim.y) * KS_ICH;
-    const int i_end = (int)((blockIdx.y + 1) * nblk / gridDim.y) * KS_ICH;
+    const int i_begin = Sliced ? (int)(blockIdx.y * nblk / gridDim.y) * KS_ICH : 0;
+    const int i_end = Sliced ? (int)((blockIdx.y + 1) * nblk / gridDim.y) * KS_ICH : RING_N;
     const uint32_t per_batch = (uint32_t)(i_end - i_begin) * KS_PAIRS;
 
     if (tid == 0) {
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
         for (int c = 0; c < KS_CPW; c++)
 #pragma unroll
             for (int q = 0; q < KS_CPT; q++)
-                acc[c][q] = (!sliced && lane + 32 * q == n) ? sm.body[warp * KS_CPW + c] : 0u;
+                acc[c][q] = (!Sliced && lane + 32 * q == n) ? sm.body[warp * KS_CPW + c] : 0u;
 
         for (int i0 = i_begin; i0 < i_end; i0 += KS_ICH) {
             if (__syncthreads_or(!ok)) {
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(KS_THREADS, 1) ks_kernel(const uint32_t *ext, 
             for (int q = 0; q < KS_CPT; q++) {
                 const int col = lane + 32 * q;
                 if (col >= V) continue;
-                if (sliced) atomicAdd(&out[(size_t)o * V + col], acc[c][q]);
+                if (Sliced) atomicAdd(&out[(size_t)o * V + col], acc[c][q]);
                 else out[(size_t)o * V + col] = acc[c][q];
             }
         }
@@ -290,7 +291,9 @@ cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int 
 {
     if (!njobs) return cudaSuccess;
     const size_t smem = sizeof(KsSmem);
-    cudaError_t e = cudaFuncSetAttribute(ks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(ks_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ks_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t nb = (njobs + KS_CT - 1) / KS_CT;
     if (2 * nb < (size_t)num_sms) {
@@ -299,12 +302,12 @@ cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int 
         const size_t total = njobs * (size_t)(n + 1);
         const int ig = (int)std::min<size_t>((total + 255) / 256, (size_t)num_sms * 8);
         ks_init_kernel<<<ig, 256, 0, st>>>(ext, jobs, njobs, dense_mux, out, n);
-        ks_kernel<<<dim3((unsigned)nb, (unsigned)slices), KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux, out, T,
-                                                                                  n, err);
+        ks_kernel<true><<<dim3((unsigned)nb, (unsigned)slices), KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux,
+                                                                                        out, T, n, err);
         return cudaGetLastError();
     }
     const int grid = (int)(nb < (size_t)num_sms ? nb : (size_t)num_sms);
-    ks_kernel<<<grid, KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux, out, T, n, err);
+    ks_kernel<false><<<grid, KS_THREADS, smem, st>>>(ext, jobs, njobs, dense_mux, out, T, n, err);
     return cudaGetLastError();
 }
 
