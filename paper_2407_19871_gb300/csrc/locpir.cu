@@ -1,4 +1,5 @@
 // Host side of liblocpir: context, key loading, the C-ABI entry points, NTT tables.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -217,6 +218,12 @@ extern "C" int lp_destroy(lp_ctx *c)
         }
     }
     tc_release(c);
+    for (cudaStream_t st : {c->st_h2d, c->st_run, c->st_d2h})
+        if (st) cudaStreamDestroy(st);
+    for (int k = 0; k < lp_ctx::HOST_CHUNKS; k++) {
+        if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+        if (c->ev_run[k]) cudaEventDestroy(c->ev_run[k]);
+    }
     for (DevBuf *b : {&c->tw_lane, &c->err, &c->bsk_hat, &c->bsk_coef, &c->ksk, &c->abar, &c->ext, &c->pool,
                       &c->jobs, &c->tmp_in, &c->tmp_out})
         free_buf(*b);
@@ -563,18 +570,49 @@ extern "C" int lp_gate_batch_host(lp_ctx *c, int op, const uint32_t *a, const ui
     int rc = ensure_buf(c->tmp_in, bytes * nin, "host-batch input staging");
     if (!rc) rc = ensure_buf(c->tmp_out, bytes, "host-batch output staging");
     if (rc) return rc;
-    uint32_t *din = static_cast<uint32_t *>(c->tmp_in.ptr);
-    const uint32_t *srcs[3] = {a, b, cc};
-    for (int k = 0; k < nin; k++) {
-        cudaError_t e = cudaMemcpyAsync(din + k * count * W, srcs[k], bytes, cudaMemcpyHostToDevice, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "copy inputs");
+    cudaError_t e = cudaSuccess;
+    if (!c->st_h2d) {
+        e = cudaStreamCreateWithFlags(&c->st_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st_run, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st_d2h, cudaStreamNonBlocking);
+        for (int k = 0; k < lp_ctx::HOST_CHUNKS && e == cudaSuccess; k++) {
+            e = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_run[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "host-batch streams");
     }
-    rc = lp_gate_batch(c, op, din, nin > 1 ? din + count * W : nullptr, nin > 2 ? din + 2 * count * W : nullptr,
-                       static_cast<uint32_t *>(c->tmp_out.ptr), count, 0);
-    if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(out, c->tmp_out.ptr, bytes, cudaMemcpyDeviceToHost, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-    if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+    // Pipeline: the batch in up to HOST_CHUNKS chunks (each still many waves of the GPU); all
+    // uploads queue on one copy stream, each chunk's gates wait for its upload, and each
+    // download waits for its gates on the other copy direction, so transfers overlap compute.
+    const size_t nch = count >= (size_t)lp_ctx::HOST_CHUNKS * 8192 ? lp_ctx::HOST_CHUNKS : 1;
+    const size_t per = (count + nch - 1) / nch;
+    uint32_t *din = static_cast<uint32_t *>(c->tmp_in.ptr);
+    uint32_t *dout = static_cast<uint32_t *>(c->tmp_out.ptr);
+    const uint32_t *srcs[3] = {a, b, cc};
+    for (size_t k = 0; k < nch && e == cudaSuccess; k++) {
+        const size_t off = k * per, cnt = std::min(per, count - off);
+        for (int i = 0; i < nin && e == cudaSuccess; i++)
+            e = cudaMemcpyAsync(din + i * count * W + off * W, srcs[i] + off * W, cnt * W * 4, cudaMemcpyHostToDevice,
+                                c->st_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[k], c->st_h2d);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy inputs");
+    for (size_t k = 0; k < nch; k++) {
+        const size_t off = k * per, cnt = std::min(per, count - off);
+        e = cudaStreamWaitEvent(c->st_run, c->ev_in[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host-batch ordering");
+        rc = lp_gate_batch(c, op, din + off * W, nin > 1 ? din + count * W + off * W : nullptr,
+                           nin > 2 ? din + 2 * count * W + off * W : nullptr, dout + off * W, cnt, c->st_run);
+        if (rc) return rc;
+        e = cudaEventRecord(c->ev_run[k], c->st_run);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st_d2h, c->ev_run[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + off * W, dout + off * W, cnt * W * 4, cudaMemcpyDeviceToHost, c->st_d2h);
+        if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+    }
+    e = cudaStreamSynchronize(c->st_d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st_run);
+    if (e != cudaSuccess) return cuda_fail(e, "host batch");
     return ctx_check_err(c);
 }
 

@@ -46,6 +46,10 @@ struct lp_ctx {
     void *blas = nullptr;           // cuBLAS handle, created on first use
     lp::DevBuf bsk_coef;            // coefficient-domain BSK (Toeplitz engine)
     lp::DevBuf tc_T, tc_D, tc_C, tc_acc, ks_A, ks_H, ks_C, ks_aux;
+    // Pipelined host-pointer batches (lp_gate_batch_host): copy and compute streams, events.
+    static constexpr int HOST_CHUNKS = 4;
+    cudaStream_t st_h2d = nullptr, st_run = nullptr, st_d2h = nullptr;
+    cudaEvent_t ev_in[HOST_CHUNKS] = {}, ev_run[HOST_CHUNKS] = {};
 };
 
 namespace lp {

@@ -67,3 +67,19 @@ def test_many_ctas_sampled(gpu_ctx, keys):
     idx = np.array([0, 1, 2, 3, 4, 401, 607, count - 1])
     assert_same(got[idx], oracle.gate_batch(keys, oracle.NAND, a[idx], b[idx]), "NAND sampled")
     np.testing.assert_array_equal(oracle.decrypt(keys.s, got), 1 - (A & B))
+
+
+def test_host_entry_point_pipelined_chunks(gpu_ctx, keys):
+    """A host batch large enough to be pipelined in chunks (uploads, gates and downloads on
+    separate streams) returns exactly what the device entry point returns; sampled rows
+    equal the oracle's."""
+    count = 4 * 8192 + 5
+    (A, B, _), (a, b, _) = _inputs(keys, 280, count)
+    out = np.empty_like(a)
+    gpu_ctx.lp_gate_batch_host(oracle.AND, a, b, None, out, count)
+    dev = empty_dev(count, keys.params.n + 1)
+    gpu_ctx.lp_gate_batch(oracle.AND, to_dev(a), to_dev(b), None, dev, count)
+    gpu_ctx.lp_sync()
+    assert_same(out, to_host(dev), "pipelined host batch vs device batch")
+    idx = np.array([0, 8193, 16387, 24581, count - 1])
+    assert_same(out[idx], oracle.gate_batch(keys, oracle.AND, a[idx], b[idx]), "pipelined host batch sampled")
