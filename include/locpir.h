@@ -253,6 +253,9 @@ int lp_autotune(lp_ctx *ctx, int *split_max_out);
  * plan's blind rotations, key switches and kernels per run. */
 typedef struct lp_plan lp_plan;
 int lp_plan_locpir(lp_ctx *ctx, const lp_query *q, size_t nq, lp_plan **out);
+/* The same for queries with server-known bounds (lp_query_known; the bounds are read during
+ * the call and fixed in the plan's circuit). */
+int lp_plan_locpir_known(lp_ctx *ctx, const lp_query_known *q, size_t nq, lp_plan **out);
 int lp_plan_run(lp_plan *plan, void *stream);
 int lp_plan_info(const lp_plan *plan, uint64_t *blind_rotations, uint64_t *key_switches, uint64_t *kernels);
 int lp_plan_destroy(lp_plan *plan);

@@ -346,30 +346,14 @@ static void plan_free(lp_plan *P)
     delete P;
 }
 
-extern "C" int lp_plan_locpir(lp_ctx *c, const lp_query *q, size_t nq, lp_plan **out)
+// Schedule a built circuit once, allocate the plan's pool and scratch, and capture the whole
+// evaluation into a CUDA graph.
+static int make_plan(lp_ctx *c, const Circuit &C, const std::vector<InputCopy> &ins,
+                     const std::vector<OutputCopy> &outs, lp_plan **out)
 {
-    int rc = check_ready(c);
-    if (rc) return rc;
-    if (!q || !out || nq == 0) return fail(LP_EINVAL, "empty or null query list");
-    *out = nullptr;
     const int n = c->params.n;
     const size_t W = (size_t)n + 1;
-    Circuit C;
-    std::vector<InputCopy> ins;
-    std::vector<OutputCopy> outs;
-    for (size_t i = 0; i < nq; i++) {
-        if ((rc = check_query(q[i]))) return rc;
-        const lp_query &Q = q[i];
-        const int x = C.inputs(Q.l), y = C.inputs(Q.l);
-        const int bx = C.inputs(4 * Q.l * Q.n_boxes);
-        const int sv = C.inputs(Q.m * Q.n_boxes);
-        ins.push_back(InputCopy{x, Q.x, Q.l});
-        ins.push_back(InputCopy{y, Q.y, Q.l});
-        ins.push_back(InputCopy{bx, Q.boxes, 4 * Q.l * Q.n_boxes});
-        ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
-        std::vector<Sig> Sv = build_locpir(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, bx, Q.m, sv, Q.comb);
-        for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{Sv[j], Q.out_service + (size_t)j * W});
-    }
+    int rc = LP_OK;
     lp_plan *P = new lp_plan();
     P->c = c;
     schedule(C, ins, outs, n, P->S);
@@ -419,6 +403,58 @@ extern "C" int lp_plan_locpir(lp_ctx *c, const lp_query *q, size_t nq, lp_plan *
     }
     *out = P;
     return LP_OK;
+}
+
+extern "C" int lp_plan_locpir(lp_ctx *c, const lp_query *q, size_t nq, lp_plan **out)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!q || !out || nq == 0) return fail(LP_EINVAL, "empty or null query list");
+    *out = nullptr;
+    const size_t W = (size_t)c->params.n + 1;
+    Circuit C;
+    std::vector<InputCopy> ins;
+    std::vector<OutputCopy> outs;
+    for (size_t i = 0; i < nq; i++) {
+        if ((rc = check_query(q[i]))) return rc;
+        const lp_query &Q = q[i];
+        const int x = C.inputs(Q.l), y = C.inputs(Q.l);
+        const int bx = C.inputs(4 * Q.l * Q.n_boxes);
+        const int sv = C.inputs(Q.m * Q.n_boxes);
+        ins.push_back(InputCopy{x, Q.x, Q.l});
+        ins.push_back(InputCopy{y, Q.y, Q.l});
+        ins.push_back(InputCopy{bx, Q.boxes, 4 * Q.l * Q.n_boxes});
+        ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
+        std::vector<Sig> Sv = build_locpir(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, bx, Q.m, sv, Q.comb);
+        for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{Sv[j], Q.out_service + (size_t)j * W});
+    }
+    return make_plan(c, C, ins, outs, out);
+}
+
+extern "C" int lp_plan_locpir_known(lp_ctx *c, const lp_query_known *q, size_t nq, lp_plan **out)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!q || !out || nq == 0) return fail(LP_EINVAL, "empty or null query list");
+    *out = nullptr;
+    const size_t W = (size_t)c->params.n + 1;
+    Circuit C;
+    std::vector<InputCopy> ins;
+    std::vector<OutputCopy> outs;
+    for (size_t i = 0; i < nq; i++) {
+        const lp_query_known &Q = q[i];
+        lp_query chk{Q.l, Q.is_signed, Q.n_boxes, Q.m, Q.comb, Q.x, Q.y, reinterpret_cast<const uint32_t *>(Q.bounds),
+                     Q.services, Q.out_service};
+        if ((rc = check_query(chk))) return rc;
+        const int x = C.inputs(Q.l), y = C.inputs(Q.l);
+        const int sv = C.inputs(Q.m * Q.n_boxes);
+        ins.push_back(InputCopy{x, Q.x, Q.l});
+        ins.push_back(InputCopy{y, Q.y, Q.l});
+        ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
+        std::vector<Sig> Sv = build_locpir_known(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, Q.bounds, Q.m, sv, Q.comb);
+        for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{Sv[j], Q.out_service + (size_t)j * W});
+    }
+    return make_plan(c, C, ins, outs, out);
 }
 
 extern "C" int lp_plan_run(lp_plan *P, void *stream)

@@ -33,6 +33,7 @@ EXPORTS = [
     "lp_server_start", "lp_server_submit", "lp_server_submit_known", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
+    "lp_plan_locpir_known",
 ]
 LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
@@ -124,6 +125,7 @@ def lib() -> ctypes.CDLL:
             "lp_load_keys_file": (i, [vp, ctypes.c_char_p]),
             "lp_sha256": (i, [vp, sz, ctypes.c_char_p]),
             "lp_plan_locpir": (i, [vp, ctypes.POINTER(lp_query), sz, ctypes.POINTER(vp)]),
+            "lp_plan_locpir_known": (i, [vp, ctypes.POINTER(lp_query_known), sz, ctypes.POINTER(vp)]),
             "lp_plan_run": (i, [vp, vp]),
             "lp_plan_info": (i, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -393,6 +395,16 @@ class Context:
         _check(lib().lp_locpir_known_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_known_batch")
 
     # ---- plans (CUDA graphs)
+    def lp_plan_locpir_known(self, queries: list[dict]) -> "Plan":
+        arr = (lp_query_known * len(queries))()
+        keep = []
+        for i, q in enumerate(queries):
+            arr[i], b = self._query_known_struct(q)
+            keep.append(b)
+        h = ctypes.c_void_p()
+        _check(lib().lp_plan_locpir_known(self.h, arr, len(queries), ctypes.byref(h)), "lp_plan_locpir_known")
+        return Plan(h, queries)
+
     def lp_plan_locpir(self, queries: list[dict]) -> "Plan":
         arr = (lp_query * len(queries))()
         for i, q in enumerate(queries):

@@ -126,3 +126,34 @@ def test_known_bounds_argument_errors(gpu_ctx):
     with pytest.raises(LocpirError):
         gpu_ctx.lp_locpir_known_batch([dict(l=4, n_boxes=0, m=1, x=x, y=x, bounds=[], services=x,
                                             out_service=empty_dev(1, n + 1))])
+
+
+def test_known_bounds_plan_replays_match_batch(gpu_ctx, keys):
+    """A known-bounds batch captured into a CUDA-graph plan gives, on every replay, the
+    ciphertexts lp_locpir_known_batch gives."""
+    n = keys.params.n
+    l, m = 8, 4
+    qs = synth.city_batch(9, 6, l, m)
+    queries, refs = [], []
+    for k, q in enumerate(qs):
+        x = _enc_bits(keys, _bits(q.x, l), 800 + k, 0)
+        y = _enc_bits(keys, _bits(q.y, l), 800 + k, l)
+        sc = _enc_bits(keys, q.service, 800 + k, 2 * l)
+        base = dict(l=l, is_signed=0, n_boxes=1, m=m, comb=C.XOR_TREE, x=to_dev(x), y=to_dev(y), bounds=[q.box],
+                    services=to_dev(sc))
+        queries.append(dict(base, out_service=empty_dev(m, n + 1)))
+        refs.append(dict(base, out_service=empty_dev(m, n + 1)))
+    gpu_ctx.lp_locpir_known_batch(refs)
+    plan = gpu_ctx.lp_plan_locpir_known(queries)
+    try:
+        for rep in range(2):
+            plan.lp_plan_run()
+            gpu_ctx.lp_sync()
+            for k, (q, r) in enumerate(zip(queries, refs)):
+                assert_same(to_host(q["out_service"]), to_host(r["out_service"]), f"replay {rep} query {k}")
+    finally:
+        plan.lp_plan_destroy()
+    for k, q in enumerate(qs):
+        x1, x2, y1, y2 = q.box
+        want = q.service if (x1 <= q.x < x2 and y1 <= q.y < y2) else np.zeros(m, np.uint8)
+        assert oracle.decrypt(keys.s, to_host(queries[k]["out_service"])).tolist() == want.tolist()
