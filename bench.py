@@ -658,6 +658,14 @@ def serve(args) -> None:
                       "wrong_bits": wrong}), flush=True)
 
 
+def workload_config(world: int) -> dict:
+    """The workload both arms report: one step is COUNT independent NAND bootstraps per rank."""
+    return {"workload": f"NAND gate bootstrapping: {COUNT:,} independent gates per step (n=630, N=1024, k=1, "
+                        "Bgbit=10, lg=3, basebit=2, t=8; keys seed 0, inputs seed 1)",
+            "global_batch": COUNT * world, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": f"inputs larger than L2 (2 x {COUNT * (N_LWE + 1) * 4 / 1e6:.0f} MB per step)"}
+
+
 def run_reference(args) -> None:
     rank, world, _ = _dist()
     if rank != 0:
@@ -679,10 +687,9 @@ def run_reference(args) -> None:
     line = {"impl": "reference", "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "NAND gate bootstrapping, 65,536 gates (n=630, N=1024, Bgbit=10, lg=3, "
-                                   "basebit=2, t=8); each reference step a bounded sample"},
+            "config": workload_config(args.gpus),
             "cpu_baseline": {"value": value, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{S} of the 65,536 NAND gates per step (OpenMP, {cores} threads)"},
+                             "sample": f"{S} of the {COUNT:,} NAND gates per step (OpenMP, {cores} threads)"},
             "e2e": {"value": value, "unit": "bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -778,10 +785,7 @@ def run_gpu(args) -> None:
         "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"NAND gate bootstrapping: {COUNT:,} independent gates per step (n=630, N=1024, k=1, "
-                               "Bgbit=10, lg=3, basebit=2, t=8; keys seed 0, inputs seed 1)",
-                   "global_batch": COUNT * world, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (2 x 165 MB per step)"},
+        "config": workload_config(world),
         "e2e": {"value": e2e_value, "unit": "bootstraps/s", "h2d_bytes_per_step": 2 * COUNT * W * 4,
                 "d2h_bytes_per_step": COUNT * W * 4},
         "gpu_launches": launches,
