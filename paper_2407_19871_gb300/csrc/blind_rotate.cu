@@ -16,9 +16,11 @@
 //   Key chunks (one chunk = row r of BSK_i for one prime, both TRLWE components, 8 KB)
 //   flow through a ring of BR_RING shared-memory slots per prime.  Lane 0 of the slot-0
 //   warp of each prime is also that prime's producer: it issues cp.async.bulk copies
-//   (TMA engine) completing on "full" mbarriers, refilling the slot released one chunk
-//   earlier (all BR_SLOTS consumers arrive on its "empty" mbarrier), i.e. BR_RING - 1
-//   chunks ahead.  All waits are bounded (LP_ETIMEOUT on expiry).
+//   (TMA engine) completing on "full" mbarriers.  After consuming chunk q it issues chunk
+//   q + BR_LOOKAHEAD into the slot of chunk q + BR_LOOKAHEAD - BR_RING = q - 2, which is
+//   free once all BR_SLOTS consumers have arrived on its "empty" mbarrier: the producer
+//   waits only for a slot that is more than one chunk behind it.  All waits are bounded
+//   (LP_ETIMEOUT on expiry).
 //
 // Per step and pair: both warps rotate/subtract ACC (shared memory) and decompose it;
 // each warp forward-transforms the 6 digit polynomials modulo its prime and multiplies
@@ -39,6 +41,8 @@ namespace lp {
 
 constexpr int BR_SLOTS = 4;
 constexpr int BR_RING = 3;
+constexpr int BR_LOOKAHEAD = 1;                          // chunks issued ahead of the one consumed
+static_assert(BR_LOOKAHEAD >= 1 && BR_LOOKAHEAD < BR_RING, "chunk q + L reuses the slot of chunk q + L - R < q");
 constexpr int BR_COMPUTE_WARPS = 2 * BR_SLOTS;
 constexpr int BR_THREADS = BR_COMPUTE_WARPS * 32;
 constexpr int CHUNK_WORDS = 2 * RING_N;                 // one (i, prime, row) chunk
@@ -149,8 +153,8 @@ __device__ __forceinline__ void mac_chunk(BrSmem &sm, int pi, int lane, bool wor
     __syncwarp();
     if (lane == 0) {
         mbar_arrive(&sm.empty_bar[pi][rs]);
-        // Refill the slot released one chunk ago (BR_RING - 1 chunks of lookahead).
-        if (producer) produce(sm, pr, cseq + BR_RING);
+        // Issue chunk cseq + BR_LOOKAHEAD (its slot held chunk cseq + BR_LOOKAHEAD - BR_RING).
+        if (producer) produce(sm, pr, cseq + 1 + BR_LOOKAHEAD);
     }
     __syncwarp();
     cseq++;
