@@ -245,6 +245,24 @@ int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
  * in flight (not while a server runs).  Results of later calls are bit-identical either way. */
 int lp_autotune(lp_ctx *ctx, int *split_max_out);
 
+/* lp_circuit_info: the gate statistics of one LocPIR query's circuit (Algorithms 2-5; the
+ * comparators of Algorithm 2, validation, bitwiseAND of Algorithm 5, the combine `comb`) as
+ * the library builds and levels it for the batch entry points, plans and the server.  With
+ * bounds == NULL the box bounds are encrypted inputs; otherwise bounds [n_boxes][4] (X1, X2,
+ * Y1, Y2; host memory, read during the call) are server-known, as in lp_query_known.  Host
+ * only: needs no context and no GPU.  *out receives:
+ *   gates_by_op[op]   bootstrapped gates per lp_op code (NOT is free and never counted);
+ *   blind_rotations   one per gate, two per MUX;  key_switches  one per gate;
+ *   levels            bootstrap depth = the number of levels the scheduler runs;
+ *   widest_level      blind rotations of the widest level;  wires  circuit wires incl. inputs.
+ * LP_EINVAL for l outside [1, 64], n_boxes < 1, m < 1, an unknown comb or a null out. */
+typedef struct lp_circuit_stats {
+    uint64_t gates_by_op[8];
+    uint64_t blind_rotations, key_switches, levels, widest_level, wires;
+} lp_circuit_stats;
+int lp_circuit_info(int l, int is_signed, int n_boxes, int m, int comb, const uint64_t *bounds,
+                    lp_circuit_stats *out);
+
 /* Plans: lp_plan_locpir schedules a batch of queries once (levels, job records, a plan-owned
  * pool and scratch) and captures the whole evaluation -- input copies from the queries' pointers,
  * every level's pre-combination / blind-rotation / key-switch pass, output copies -- into one

@@ -326,6 +326,43 @@ extern "C" int lp_locpir_known_batch(lp_ctx *c, const lp_query_known *q, size_t 
 }
 
 // ---------------------------------------------------------------------------------
+// Gate statistics of one query's circuit, host only (no context, no device call).
+extern "C" int lp_circuit_info(int l, int is_signed, int n_boxes, int m, int comb, const uint64_t *bounds,
+                               lp_circuit_stats *out)
+{
+    if (!out) return fail(LP_EINVAL, "null output pointer");
+    if (l < 1 || l > 64) return fail(LP_EINVAL, "bit width l=%d outside [1, 64]", l);
+    if (n_boxes < 1) return fail(LP_EINVAL, "n_boxes=%d < 1", n_boxes);
+    if (m < 1) return fail(LP_EINVAL, "service length m=%d < 1", m);
+    if (comb < LP_XOR_TREE || comb > LP_OR_TREE) return fail(LP_EINVAL, "unknown combine %d", comb);
+    Circuit C;
+    const int x = C.inputs(l), y = C.inputs(l);
+    if (bounds) {
+        const int sv = C.inputs(m * n_boxes);
+        build_locpir_known(C, l, is_signed != 0, x, y, n_boxes, bounds, m, sv, comb);
+    } else {
+        const int bx = C.inputs(4 * l * n_boxes);
+        const int sv = C.inputs(m * n_boxes);
+        build_locpir(C, l, is_signed != 0, x, y, n_boxes, bx, m, sv, comb);
+    }
+    lp_circuit_stats st{};
+    for (const Node &nd : C.nodes) {
+        st.gates_by_op[nd.op]++;
+        st.blind_rotations += nd.op == LP_MUX ? 2 : 1;
+    }
+    st.key_switches = C.nodes.size();
+    const std::vector<std::vector<int>> lv = levels_of(C);
+    for (size_t d = 1; d < lv.size(); d++) {
+        uint64_t br = 0;
+        for (int g : lv[d]) br += C.nodes[g].op == LP_MUX ? 2 : 1;
+        if (!lv[d].empty()) st.levels++;
+        st.widest_level = std::max(st.widest_level, br);
+    }
+    st.wires = C.depth.size();
+    *out = st;
+    return LP_OK;
+}
+
 // Plans: a LocPIR batch scheduled once and captured into a CUDA graph.
 // ---------------------------------------------------------------------------------
 struct lp_plan {

@@ -33,7 +33,7 @@ EXPORTS = [
     "lp_server_start", "lp_server_submit", "lp_server_submit_known", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
-    "lp_plan_locpir_known",
+    "lp_plan_locpir_known", "lp_circuit_info",
 ]
 LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
@@ -61,6 +61,11 @@ class lp_stats(ctypes.Structure):
                                                "ticks", "bootstraps")] + \
                [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "elapsed_s", "queries_per_s",
                                                "bootstraps_per_s")]
+
+
+class lp_circuit_stats(ctypes.Structure):
+    _fields_ = [("gates_by_op", ctypes.c_uint64 * 8)] + \
+               [(k, ctypes.c_uint64) for k in ("blind_rotations", "key_switches", "levels", "widest_level", "wires")]
 
 
 class LocpirError(RuntimeError):
@@ -132,6 +137,7 @@ def lib() -> ctypes.CDLL:
             "lp_plan_destroy": (i, [vp]),
             "lp_set_engines": (i, [vp, i, i]),
             "lp_autotune": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
+            "lp_circuit_info": (i, [i, i, i, i, i, vp, ctypes.POINTER(lp_circuit_stats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -176,6 +182,20 @@ def params_default() -> lp_params:
     p = lp_params()
     _check(lib().lp_params_default(ctypes.byref(p)), "lp_params_default")
     return p
+
+
+def lp_circuit_info(l, is_signed, n_boxes, m, comb=LP_XOR_TREE, bounds=None) -> dict:
+    """Gate statistics of one LocPIR query's circuit as the library builds and levels it (host
+    only).  bounds: None (encrypted bounds) or [n_boxes][4] server-known (X1, X2, Y1, Y2)."""
+    st = lp_circuit_stats()
+    b = None
+    if bounds is not None:
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.uint64).reshape(n_boxes, 4))
+    _check(lib().lp_circuit_info(l, int(is_signed), n_boxes, m, comb, None if b is None else b.ctypes.data,
+                                 ctypes.byref(st)), "lp_circuit_info")
+    return {"gates_by_op": list(st.gates_by_op), "blind_rotations": st.blind_rotations,
+            "key_switches": st.key_switches, "levels": st.levels, "widest_level": st.widest_level,
+            "wires": st.wires}
 
 
 def lp_client_lwe_encrypt(n, s, mask, noise, mu, out, count, stream=None):
