@@ -85,6 +85,9 @@ def test_closed_forms(l, nb, m):
     assert s["levels"] == l + 1 + 2 + 1 + math.ceil(math.log2(nb))
     assert s["gates_by_op"][C.XNOR] == 4 * l * nb and s["gates_by_op"][MUX] == 4 * l * nb
     assert s["widest_level"] == max(4 * l * nb, nb * m, 8 * nb)
+    # Wires: the inputs, one per bootstrapped gate and the shared trivial zero (Enc(0) of
+    # Algorithm 2) -- the closed form the query server reserves pool space with.
+    assert s["wires"] == 2 * l + 4 * l * nb + m * nb + s["key_switches"] + 1
     chain = _lib_info(l, False, nb, m, C.XOR_CHAIN)
     assert chain["blind_rotations"] == nb * (12 * l + 3 + m) + nb * m
     assert chain["levels"] == l + 1 + 2 + 1 + nb
