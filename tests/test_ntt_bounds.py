@@ -45,6 +45,16 @@ def test_lazy_forward_transform_and_mac_fit_their_words(p):
     assert 2 * p < 2 ** 32
 
 
+@pytest.mark.parametrize("p", PRIMES)
+def test_split_kernel_per_product_reduction_bounds(p):
+    """The split blind rotation reduces each product on its own: x < 22p and a key word < p give
+    x k < 22 p^2 < 2^32 p, so the Montgomery result lies in [0, 2p); the 6 digit rows' results
+    summed in shared memory stay below 12p < 2^32."""
+    assert 22 * p * p < 2 ** 32 * p
+    assert ((22 * p - 1) * (p - 1) + (2 ** 32 - 1) * p) // 2 ** 32 < 2 * p
+    assert 6 * 2 * p < 2 ** 32
+
+
 def test_centred_crt_range_covers_every_product():
     """|sum_r sum_j d * b| <= (k+1) lg * N * (Bg/2) * 2^31 with digits in [-Bg/2, Bg/2) and
     key words centred in [-2^31, 2^31): the two-prime product must exceed twice that bound so
