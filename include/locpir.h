@@ -287,8 +287,9 @@ int lp_plan_destroy(lp_plan *plan);
  * key switch), so queries of different shapes and depths share batches.  policy LP_SERVER_QUEUE
  * keeps queries that do not fit waiting; LP_SERVER_REJECT refuses them with LP_EBUSY.  Scratch for
  * the shared batches is allocated outside the budget.  Results are bit-identical to
- * lp_locpir_query on the same query.  While a server runs, its context's other evaluation calls
- * may still be used from other threads only on other contexts.
+ * lp_locpir_query on the same query.  While a server runs, call no other evaluation entry point
+ * on its context (other contexts may be used from other threads); submit, poll, wait and stats
+ * are safe from any thread.
  * lp_server_submit: the query's device pointers (inputs and out_service) must stay valid until the
  * query is done; *ticket identifies it.  A query larger than the whole budget returns LP_EBUSY.
  * lp_server_poll: *done = 1 once out_service holds the result.  lp_server_wait: block up to

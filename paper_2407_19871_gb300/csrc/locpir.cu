@@ -316,7 +316,7 @@ extern "C" int lp_reset_timing(lp_ctx *c)
     return LP_OK;
 }
 
-extern "C" uint64_t lp_launch_count(const lp_ctx *c) { return c ? c->launches : 0; }
+extern "C" uint64_t lp_launch_count(const lp_ctx *c) { return c ? c->launches.load() : 0; }
 
 // ---------------------------------------------------------------------------------
 // Keys.

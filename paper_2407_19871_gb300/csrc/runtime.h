@@ -1,5 +1,6 @@
 // Context structure and host helpers of liblocpir (internal).
 #pragma once
+#include <atomic>
 #include <map>
 #include <string>
 #include <utility>
@@ -37,7 +38,7 @@ struct lp_ctx {
     lp::DevBuf tmp_in, tmp_out;     // staging of the host-pointer entry points
     bool have_bsk = false, have_ksk = false;
     bool timing = false;
-    uint64_t launches = 0;
+    std::atomic<uint64_t> launches{0};   // incremented by the server thread too
     std::map<std::string, lp::KernelTimer> timers;
     lp::Server *server = nullptr;   // query server (lp_server_start), if running
     // Alternative tensor-core engines (tensor_engine.cu) and their state.

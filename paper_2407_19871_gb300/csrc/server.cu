@@ -175,6 +175,7 @@ static int tick(Server &S)
     std::vector<Pass> passes;
     Pass ps{0, 0, 0, 0};
     size_t max_pass = 1;
+    uint64_t tick_bootstraps = 0;
     for (SrvQuery *Q : S.active) {
         if (Q->next_level >= (int)Q->levels.size()) continue;
         const int base = (int)(Q->pool_off / W);
@@ -236,7 +237,7 @@ static int tick(Server &S)
                           S.st);
         c->launches += 3;
         if (e != cudaSuccess) return cuda_fail(e, "server: pass launch");
-        S.bootstraps += p.br_cnt;
+        tick_bootstraps += p.br_cnt;
     }
     if (!outc.empty()) {
         e = launch_copy_entries(reinterpret_cast<const CopyEntry *>(jb + out_off), outc.size(), n, c->num_sms, S.st);
@@ -246,9 +247,11 @@ static int tick(Server &S)
     for (SrvQuery *Q : S.active) Q->next_level++;
     e = cudaStreamSynchronize(S.st);
     if (e != cudaSuccess) return cuda_fail(e, "server: tick");
-    S.ticks++;
     const auto now = Clock::now();
+    // Counters that lp_server_stats reads are updated under the lock.
     std::lock_guard<std::mutex> lock(S.mu);
+    S.ticks++;
+    S.bootstraps += tick_bootstraps;
     for (SrvQuery *Q : finishing) {
         Q->done = true;
         Q->t_done = now;
