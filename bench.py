@@ -535,7 +535,8 @@ def paper_shapes() -> None:
             # Phases, each batch timed on its own, with the gate counts and depths of the query's own
             # phases: the 36 comparators (4 per box) as one batch (LT(a, b) = NOT LE(b, a), and NOT
             # costs no bootstrap), validation (3 ANDs per box, 2 levels), services (9 x 9 bitwise
-            # AND) and the 8 levels of the XOR chain.
+            # AND) and the 9 levels of the XOR chain (Algorithm 4 starts from S = Enc(0)^m, so box 1's
+            # services are XORed into the trivial zero too).
             cx1 = bx.view(9, 4, l, W)
             pt = torch.cat([x.expand(9, l, W), y.expand(9, l, W)]).reshape(-1, W)
             a_le = torch.cat([cx1[:, 0], cx1[:, 2], cx1[:, 1], cx1[:, 3]]).reshape(-1, W).contiguous()
@@ -550,7 +551,7 @@ def paper_shapes() -> None:
             svc = _encrypt_bits(p, s_dev, synth.bits(9, 2, 81), 10)
             t_svc = _timed(lambda: ctx.lp_gate_batch(locpir.LP_AND, svc, svc, None, svc.clone(), 81))
             t_xor = _timed(lambda: [ctx.lp_gate_batch(locpir.LP_XOR, svc[:9], svc[9:18], None, svc[18:27].clone(), 9)
-                                    for _ in range(8)])
+                                    for _ in range(9)])
             ph = torch.empty(m, dtype=torch.int32, device="cuda")
             locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, m)
             got = sum(int(b > 0) << j for j, b in enumerate(ph.cpu().numpy()))
