@@ -75,3 +75,44 @@ def test_zero_count_is_noop(gpu_ctx, keys):
     gpu_ctx.lp_gate_batch(0, t, t, None, t, 0)
     gpu_ctx.lp_bootstrap_extract(t, EIGHTH, empty_dev(1, p.N + 1), 0)
     gpu_ctx.lp_sync()
+
+
+# ---------------------------------------------------------------------------------------
+# The edge of the product engine's exactness (tests/crt_edge.py): key words at -2^31 and
+# body digits at -512 drive the first external product to 3 * 2^50 ~ 2^51.6 (random inputs
+# reach ~2^46), near the 2^52.6 bound the centred two-prime CRT must cover.  TFHE's external
+# product (J. Cryptology 2020), to which the paper's EvalGate (Section 2.2) defers.
+# ---------------------------------------------------------------------------------------
+@pytest.fixture(scope="module", params=[0, 24], ids=["key-0x80000000", "key-low-bits-24"])
+def edge_case(request):
+    from crt_edge import crafted_bsk
+    from paper_2407_19871_gb300 import build
+    from paper_2407_19871_gb300.locpir import Context
+    p = synth.DEFAULT
+    bsk = crafted_bsk(p, low_bits=request.param, seed=17)
+    keys = oracle.Keys(p, np.zeros(p.n, np.uint8), np.zeros(p.N, np.uint8), bsk, np.zeros(1, np.uint32))
+    build.build()
+    ctx = Context(0)
+    ctx.lp_load_bsk(np.ascontiguousarray(bsk.reshape(-1)))
+    yield ctx, keys
+    ctx.close()
+
+
+@pytest.mark.parametrize("engine", ["batched", "split"])
+@pytest.mark.parametrize("count", [1, 7])
+def test_bootstrap_at_the_crt_edge_matches_oracle(edge_case, engine, count):
+    """count = 7: one full group of 4 and a ragged group of 3 on the batched kernel; sample 0
+    has one edge step, sample 1 all 630, the others a random subset."""
+    from crt_edge import MU_EDGE, crafted_lwes
+    from paper_2407_19871_gb300.locpir import LP_BR_NTT, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT
+    ctx, keys = edge_case
+    p = keys.params
+    lwe = crafted_lwes(p, count, seed=40 + count)
+    ctx.lp_set_engines(LP_BR_NTT_BATCHED if engine == "batched" else LP_BR_NTT_SPLIT, 0)
+    try:
+        ext = empty_dev(count, p.N + 1)
+        ctx.lp_bootstrap_extract(to_dev(lwe), MU_EDGE, ext, count)
+        ctx.lp_sync()
+    finally:
+        ctx.lp_set_engines(LP_BR_NTT, 0)
+    assert_same(to_host(ext), oracle.bootstrap_extract(keys, lwe, mu=MU_EDGE), f"edge {engine} x{count}")
