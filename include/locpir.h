@@ -132,7 +132,7 @@ int lp_gate_batch(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, con
 int lp_gate_batch_host(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
                        uint32_t *out, size_t count);
 
-/* lp_gate_batch_noalloc: the same gates as lp_gate_batch, computed by the same kernels, for
+/* lp_gate_batch_noalloc: the same gates as lp_gate_batch, bit for bit, for
  * callers that must not allocate device memory while they evaluate -- e.g. a server whose
  * device memory is handed out up front by its own allocator and budget, or a latency-critical
  * loop that cannot absorb the device-wide synchronisation of cudaMalloc / cudaFree.  (The
@@ -146,7 +146,12 @@ int lp_gate_batch_host(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b
  * that first call before any stream capture.  All calls share the array and it keeps the last
  * call's contents (nothing in it needs clearing: every word read is written earlier in the same
  * call), so calls that overlap on the GPU race: issue them in order on one stream.  Keys must be
- * loaded (LP_ENOKEY otherwise); pointers and layout as in lp_gate_batch. */
+ * loaded (LP_ENOKEY otherwise); pointers and layout as in lp_gate_batch.
+ * Kernels: always the NTT blind rotation and the table key switch.  A forced split or batched
+ * NTT choice (lp_set_engines) is honoured; a tensor-core engine selection is ignored here,
+ * because those engines allocate their scratch.  The per-phase timers are not recorded.
+ * A device reset (cudaDeviceReset) after the first call invalidates the looked-up address:
+ * the entry point then stays unusable on that device until the process restarts. */
 int lp_gate_batch_noalloc(lp_ctx *ctx, int op, const uint32_t *a, const uint32_t *b, const uint32_t *c,
                           uint32_t *out, size_t count, void *stream);
 
