@@ -34,14 +34,30 @@ N_LWE, N_RING = 630, 1024
 # two NTT primes x (6 forward + 2 inverse length-1024 transforms x 5,120 butterflies +
 # 12 x 1,024 pointwise products) = 2 x 53,248.
 MODMUL_PER_STEP = 2 * ((6 + 2) * 5120 + 12 * 1024)
-# Peak modmul rate derived from unit counts and clocks: 152 SMs x 2,070 MHz x 64 integer
-# multiply-adds per SM per clock / 3 multiply-adds per Shoup modular multiplication.
-SMS, MAX_MHZ, IMAD_PER_CLK_SM, IMAD_PER_MODMUL = 152, 2070.0, 64, 3
-PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * IMAD_PER_CLK_SM / IMAD_PER_MODMUL
-# The same peak with the measured cost of one lazy Shoup product on GB300 (16.0 per SM per
-# clock: its multiply-high runs at half rate), from paper_2407_19871_gb300/peaks/int_peaks.cu.
-MEASURED_SHOUP_PER_CLK_SM = 16.0
-MEASURED_PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * MEASURED_SHOUP_PER_CLK_SM
+# Peak modmul rate from unit counts and clocks: 152 SMs x 2,070 MHz x 64 integer-multiply
+# pipe slots per SM per clock / 4 slots per lazy Shoup product (y w and q p take one slot each,
+# the multiply-high q = mulhi(y, w') two, as it runs at half rate).  The rate measured on GB300
+# agrees: 16.0 Shoup products per SM per clock (bench_int_peaks.cu, `bench.py --int-peaks`).
+SMS, MAX_MHZ, IMAD_PER_CLK_SM = 152, 2070.0, 64
+SLOTS_PER_SHOUP = 4
+PEAK_MODMUL_PER_S = SMS * MAX_MHZ * 1e6 * IMAD_PER_CLK_SM / SLOTS_PER_SHOUP
+# Charging the multiply-high one slot only (3 per product) gives a higher, unreachable figure;
+# reported as a labelled note.
+PEAK_MODMUL_3_SLOT = SMS * MAX_MHZ * 1e6 * IMAD_PER_CLK_SM / 3
+# Key switch (table gather-accumulate): algorithmic DRAM bytes per launch are the digit-pair
+# table once plus the extracted inputs and the outputs; its own floor is shared-memory
+# bandwidth, one 4-byte table read per output word and digit pair, 128 B/clock/SM.
+KS_TABLE_BYTES = 1024 * 4 * 16 * 632 * 4
+# Blind rotation: the transform-domain key once per launch (n x 2 primes x 6 rows x 2 x N
+# words), plus per ciphertext its mod-switched inputs (632 u16) and its extracted sample
+# (1028 u32).
+BR_KEY_BYTES = N_LWE * 2 * 6 * 2 * N_RING * 4
+BR_BYTES_PER_CT = 632 * 2 + 1028 * 4
+BR_TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one br_kernel launch on a small case "
+                   "(profiles/traffic.json), scaled to this launch as key + per-ciphertext bytes x ciphertexts; "
+                   "null once the kernel sources differ from the captured ones")
+KS_SMEM_BYTES_PER_CT = 1024 * 4 * 632 * 4
+SMEM_BYTES_PER_CLK_SM = 128
 
 
 def _dist():
@@ -224,6 +240,31 @@ def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2) -> dict:
                      "CUDA-graph plan"}
 
 
+def single_query_latency(ctx, p, s_dev) -> dict:
+    """The single-query workload: 16-bit unsigned fixed-point coordinates (Seoul's Table 1 box
+    and a point inside it, shifted by +90 / +180 degrees, 7 fraction bits), one box, a 64-bit
+    service holding 427, encrypted under the seed-0 keys with seed-0 draws.  Median time of
+    lp_locpir_query over 3 runs after a warm-up; the decrypted service is checked."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    l, m = 16, 64
+    enc = lambda deg: int(np.floor(deg * 128 + 0.5))
+    box = (enc(37.4758 + 90), enc(37.6195 + 90), enc(126.8831 + 180), enc(127.1331 + 180))
+    px, py = enc(37.55 + 90), enc(127.0 + 180)
+    bits = np.concatenate([synth.int_to_bits(px, l), synth.int_to_bits(py, l)] +
+                          [synth.int_to_bits(v, l) for v in box] + [synth.int_to_bits(427, m)])
+    ct = _encrypt_bits(p, s_dev, bits, 0)
+    out = torch.empty(m, p.n + 1, dtype=torch.int32, device="cuda")
+    run = lambda: ctx.lp_locpir_query(l, 0, ct[:l], ct[l:2 * l], 1, ct[2 * l:6 * l], m, ct[6 * l:],
+                                      locpir.LP_XOR_TREE, out)
+    sec = _timed(run)
+    ph = torch.empty(m, dtype=torch.int32, device="cuda")
+    locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, m)
+    got = sum(int(b > 0) << j for j, b in enumerate(ph.cpu().numpy()))
+    return {"ms_per_query": sec * 1e3, "blind_rotations": 12 * l + 3 + m, "result": got, "expected": 427,
+            "shape": "1 query, l=16 unsigned, 1 box (Seoul), m=64, keys and draws seed 0"}
+
+
 def known_bounds_throughput(ctx, p, s_dev, nq: int, seed: int = 5) -> dict:
     """City-shaped queries (l = 32 unsigned, one box, m = 256) evaluated twice through the
     batch entry points: with the box bounds encrypted (lp_locpir_batch) and known to the
@@ -359,6 +400,17 @@ def br_latency_bench() -> None:
     ctx.close()
 
 
+def int_peaks() -> int:
+    """Build and run bench_int_peaks.cu, the integer-pipe throughput microbenchmark behind the
+    "alu" roofline's peak: one JSON line of operations per SM per clock for each pattern."""
+    from paper_2407_19871_gb300.build import ARCH, nvcc
+    out_dir = os.path.join(ROOT, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "bench_int_peaks")
+    subprocess.check_call([nvcc(), os.path.join(ROOT, "bench_int_peaks.cu"), "-o", exe, "-O3"] + ARCH)
+    return subprocess.call([exe])
+
+
 def check_outputs(p, s_dev, out, A, B) -> int:
     import torch
     from paper_2407_19871_gb300 import locpir
@@ -387,8 +439,15 @@ def cpu_baseline(seconds_target: float = 15.0) -> dict:
     t0 = time.perf_counter()
     oracle.gate_batch(keys, oracle.NAND, a, b, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on the first few gates
+    S1 = 4
+    t0 = time.perf_counter()
+    oracle.gate_batch(keys, oracle.NAND, a[:S1], b[:S1], nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": S / dt, "unit": "bootstraps/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {S} of the 65,536 NAND gates (OpenMP over gates, {cores} threads), {dt:.1f} s"}
+            "sample": f"first {S} of the 65,536 NAND gates (OpenMP over gates, {cores} threads), {dt:.1f} s",
+            "single_thread_value": S1 / dt1,
+            "single_thread_sample": f"first {S1} gates on 1 thread, {dt1:.1f} s"}
 
 
 def kernel_source_sha256(spec: list[str]) -> str:
@@ -406,17 +465,29 @@ def kernel_source_sha256(spec: list[str]) -> str:
     return h.hexdigest()
 
 
-def br_traffic():
-    """DRAM bytes per blind-rotation launch from the recorded ncu capture, or None once the
-    kernel sources differ from the ones the counters were taken on."""
+def br_traffic(count: int):
+    """DRAM bytes of one blind-rotation launch over `count` ciphertexts, from the small-case
+    ncu capture recorded in profiles/traffic.json: the key once, plus the capture's bytes per
+    ciphertext beyond the key times `count`.  None once the kernel sources differ from the
+    ones the counters were taken on."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        if kernel_source_sha256(rec["source_files"]) != rec["br_kernel_source_sha256"]:
+        if kernel_source_sha256(rec["source_files"]) != rec["source_sha256"]:
             return None
-        return rec["br_kernel_dram_bytes_per_launch"]
+        small = rec["br_kernel"]["small_case"]
+        per_ct = (small["dram_bytes"] - BR_KEY_BYTES) / small["ciphertexts"]
+        return int(BR_KEY_BYTES + per_ct * count)
     except Exception:
         return None
+
+
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 # ---------------------------------------------------------------------------------------
@@ -592,6 +663,96 @@ def paper_shapes() -> None:
                                   "seconds": r["seconds"], "wrong_bits": r["wrong_bits"],
                                   "wrong_queries": r["wrong_queries"]}), flush=True)
         ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# The multi-box uneven batch: 1,024 queries, B_x ~ U{1..128}, l ~ U{16, 24, 32}, m = 512,
+# per-box results combined by an encrypted OR tree, run in memory-budgeted waves.
+# ---------------------------------------------------------------------------------------
+def multibox_uneven(args) -> None:
+    """Queries from synth.multibox_batch(3, nq) (m = 512).  Input ciphertexts are gathered on the
+    device from a pool of 65,536 fresh encryptions of random bits (synth draws, seed 3): each
+    input bit of a query takes a pool ciphertext of the same bit, so every blind rotation runs all
+    of its steps on a real encryption.  Queries go to lp_locpir_batch_waves in chunks whose
+    inputs are gathered before the chunk's timed region; each chunk runs in waves whose circuits
+    fit the memory budget.  Every output bit is decrypted and checked against the plaintext
+    truth (OR of the services of the boxes holding the point).  One JSON line."""
+    import torch
+    from paper_2407_19871_gb300 import locpir
+    ctx, p, s_dev, _, _ = setup_gpu(0, count=1)
+    W = p.n + 1
+    nq, m = args.multibox_queries, 512
+    qs = synth.multibox_batch(3, nq, m=m)
+    P = 1 << 16
+    pool_bits = synth.bits(3, 900, P)
+    pool = _encrypt_bits(p, s_dev, pool_bits, 3)
+    zeros, ones = np.flatnonzero(pool_bits == 0), np.flatnonzero(pool_bits == 1)
+    total_br = sum(locpir.lp_circuit_info(q.l, 0, len(q.boxes), m, locpir.LP_OR_TREE)["blind_rotations"] for q in qs)
+    budget = int(args.multibox_budget_gb * 2**30)
+    ctx.lp_reset_timing()
+    ctx.lp_set_timing(True)
+    seconds, waves, wrong_bits, wrong_queries, chunks = 0.0, 0, 0, [], 0
+    k0 = 0
+    while k0 < nq:
+        # a chunk: queries whose gathered inputs fit the input budget
+        k1, cnt = k0, 0
+        while k1 < nq:
+            q = qs[k1]
+            c = 2 * q.l + len(q.boxes) * (4 * q.l + m)
+            if k1 > k0 and (cnt + c) * W * 4 > args.multibox_input_gb * 2**30:
+                break
+            cnt += c
+            k1 += 1
+        bits = np.concatenate([np.concatenate([synth.int_to_bits(q.x, q.l), synth.int_to_bits(q.y, q.l)] +
+                                              [synth.int_to_bits(v, q.l) for b in q.boxes for v in b] +
+                                              [np.asarray(q.services, np.uint8).reshape(-1)]) for q in qs[k0:k1]])
+        h = (np.arange(len(bits), dtype=np.uint64) * np.uint64(2654435761) + np.uint64(977 * k0)) % np.uint64(1 << 32)
+        idx = np.where(bits == 1, ones[h % np.uint64(len(ones))], zeros[h % np.uint64(len(zeros))])
+        ct = pool.index_select(0, torch.from_numpy(idx.astype(np.int64)).cuda())
+        out = torch.empty((k1 - k0) * m, W, dtype=torch.int32, device="cuda")
+        batch, off = [], 0
+        for j, q in enumerate(qs[k0:k1]):
+            l, nb = q.l, len(q.boxes)
+            c = 2 * l + nb * (4 * l + m)
+            d = ct[off:off + c]
+            batch.append(dict(l=l, is_signed=0, n_boxes=nb, m=m, comb=locpir.LP_OR_TREE, x=d[:l], y=d[l:2 * l],
+                              boxes=d[2 * l:2 * l + 4 * l * nb], services=d[2 * l + 4 * l * nb:],
+                              out_service=out[j * m:(j + 1) * m]))
+            off += c
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        waves += ctx.lp_locpir_batch_waves(batch, budget)
+        torch.cuda.synchronize()
+        seconds += time.perf_counter() - t0
+        ph = torch.empty(out.shape[0], dtype=torch.int32, device="cuda")
+        locpir.lp_client_lwe_phase(p.n, s_dev, out, ph, out.shape[0])
+        got = (ph.cpu().numpy() > 0).astype(np.uint8).reshape(k1 - k0, m)
+        for j, q in enumerate(qs[k0:k1]):
+            want = np.zeros(m, np.uint8)
+            for (x1, x2, y1, y2), sv in zip(q.boxes, np.asarray(q.services, np.uint8).reshape(-1, m)):
+                if x1 <= q.x < x2 and y1 <= q.y < y2:
+                    want |= sv
+            bad = int((got[j] != want).sum())
+            wrong_bits += bad
+            if bad:
+                wrong_queries.append(k0 + j)
+        del ct, out, batch
+        chunks += 1
+        k0 = k1
+    br_ms, _ = ctx.lp_kernel_time("br")
+    ks_ms, _ = ctx.lp_kernel_time("ks")
+    ctx.lp_set_timing(False)
+    hist = {}
+    for q in qs:
+        hist[q.l] = hist.get(q.l, 0) + 1
+    print(json.dumps({"experiment": "multibox_uneven", "queries": nq, "m": m, "comb": "OR tree",
+                      "boxes_mean": float(np.mean([len(q.boxes) for q in qs])), "widths": hist,
+                      "blind_rotations": total_br, "seconds": seconds, "queries_per_s": nq / seconds,
+                      "blind_rotations_per_s": total_br / seconds, "br_kernel_s": br_ms / 1e3, "ks_kernel_s": ks_ms / 1e3,
+                      "chunks": chunks, "waves": waves, "memory_budget_gb": args.multibox_budget_gb,
+                      "wrong_bits": wrong_bits, "wrong_queries": len(wrong_queries),
+                      "wrong_query_ids": wrong_queries[:32], "split_max": ctx.split_max}), flush=True)
+    ctx.close()
 
 
 # ---------------------------------------------------------------------------------------
@@ -787,17 +948,23 @@ def run_gpu(args) -> None:
             torch.cuda.synchronize()
         per_gate = k / (time.perf_counter() - g0)
 
-    loc = None
+    loc = single = None
     if rank == 0 and args.locpir_queries > 0:
         loc = locpir_throughput(ctx, p, s_dev, args.locpir_queries)
+        single = single_query_latency(ctx, p, s_dev)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     br_avg_ms = br_ms / max(br_n, 1)
+    ks_avg_ms = ks_ms / max(ks_n, 1)
     achieved = COUNT * N_LWE * MODMUL_PER_STEP / (br_avg_ms / 1e3)
-    traffic = br_traffic()
+    traffic = br_traffic(COUNT)
+    peaks = _measured_peaks()
+    ks_bytes = KS_TABLE_BYTES + COUNT * (4 * 1028 + 4 * W)
+    ks_gbs = ks_bytes / (ks_avg_ms / 1e3) / 1e9 if ks_avg_ms > 0 else None
+    smem_floor_ms = COUNT * KS_SMEM_BYTES_PER_CT / (SMEM_BYTES_PER_CLK_SM * SMS * MAX_MHZ * 1e6) * 1e3
     line = {
         "metric": "gate bootstraps/s", "value": value, "unit": "bootstraps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -809,14 +976,22 @@ def run_gpu(args) -> None:
         "roofline": {"bound": "alu", "kernel": "br_kernel (blind rotation + extraction)",
                      "achieved": achieved / 1e12, "peak": PEAK_MODMUL_PER_S / 1e12, "unit": "Tmodmul/s",
                      "frac": achieved / PEAK_MODMUL_PER_S, "traffic": traffic,
-                     "peak_measured_shoup": MEASURED_PEAK_MODMUL_PER_S / 1e12,
-                     "frac_of_measured_shoup": achieved / MEASURED_PEAK_MODMUL_PER_S,
-                     "br_ms_per_launch": br_avg_ms, "ks_ms_per_launch": ks_ms / max(ks_n, 1)},
+                     "algorithmic_bytes": BR_KEY_BYTES + COUNT * BR_BYTES_PER_CT,
+                     "traffic_source": BR_TRAFFIC_NOTE,
+                     "peak_source": "152 SMs x 2070 MHz x 64 multiply-pipe slots / 4 slots per lazy Shoup "
+                                    "product; measured 16.0 Shoup products per SM per clock",
+                     "peak_3_slot_note": PEAK_MODMUL_3_SLOT / 1e12,
+                     "br_ms_per_launch": br_avg_ms, "ks_ms_per_launch": ks_avg_ms},
+        "ks": {"kernel": "ks_kernel (digit-pair table gather-accumulate)", "ms_per_launch": ks_avg_ms,
+               "algorithmic_bytes": ks_bytes, "achieved_gbs": ks_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+               "hbm_frac": (ks_gbs / peaks["hbm_gbs"]) if ks_gbs and peaks.get("hbm_gbs") else None,
+               "smem_floor_ms": smem_floor_ms, "frac_of_smem_floor": smem_floor_ms / ks_avg_ms if ks_avg_ms else None},
         "clocks": clk,
         "per_gate_bootstraps_per_s": per_gate,
         "batched_speedup_vs_per_gate": (value / world / per_gate) if per_gate else None,
         "decrypt_errors": wrong,
         "locpir": loc,
+        "single_query": single,
         "autotune": {"split_max": ctx.split_max},
     }
     if args.cpu_baseline:
@@ -846,6 +1021,13 @@ def main():
     ap.add_argument("--br-latency", action="store_true",
                     help="blind-rotation time against level width, batched and split kernels")
     ap.add_argument("--engines-ks-count", type=int, default=65536)
+    ap.add_argument("--multibox", action="store_true",
+                    help="the uneven multi-box batch (1,024 queries, B_x ~ U{1..128}, l ~ U{16,24,32}, m=512, OR tree)")
+    ap.add_argument("--multibox-queries", type=int, default=1024)
+    ap.add_argument("--multibox-budget-gb", type=float, default=96.0)
+    ap.add_argument("--multibox-input-gb", type=float, default=32.0)
+    ap.add_argument("--int-peaks", action="store_true",
+                    help="integer-pipe throughput microbenchmark (the alu roofline's measured peak)")
     ap.add_argument("--serve-shape", default="uneven", choices=["uneven", "city"])
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -857,7 +1039,11 @@ def main():
                     help="gates per step (default 65,536; smaller values are for profiling only)")
     args = ap.parse_args()
     COUNT = args.count
-    if args.paper_shapes:
+    if args.int_peaks:
+        sys.exit(int_peaks())
+    if args.multibox:
+        multibox_uneven(args)
+    elif args.paper_shapes:
         paper_shapes()
     elif args.serve:
         serve(args)

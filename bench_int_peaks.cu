@@ -6,8 +6,7 @@
 // Every thread runs 8 independent dependency chains so that latency is hidden; 8 warps per
 // SM sub-partition.  The results are the measured denominators behind the "alu" roofline.
 //
-// Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o int_peaks int_peaks.cu
-// Run:   ./int_peaks        (prints one JSON object)
+// Build and run: python bench.py --int-peaks   (prints one JSON object)
 #include <cstdio>
 #include <cstdint>
 #include <cuda_runtime.h>

@@ -38,16 +38,19 @@ def test_traffic_is_reported_only_for_unchanged_sources(tmp_path, monkeypatch):
     _copy_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     rec = json.load(open(tmp_path / "profiles" / "traffic.json"))
-    recorded = rec["br_kernel_dram_bytes_per_launch"]
+    small = rec["br_kernel"]["small_case"]
     # Make the record describe the copied sources, then change one line of the kernel region.
-    rec["br_kernel_source_sha256"] = bench.kernel_source_sha256(rec["source_files"])
+    rec["source_sha256"] = bench.kernel_source_sha256(rec["source_files"])
     json.dump(rec, open(tmp_path / "profiles" / "traffic.json", "w"))
-    assert bench.br_traffic() == recorded
+    # the capture itself reproduces, and a larger launch adds the per-ciphertext bytes only
+    assert abs(bench.br_traffic(small["ciphertexts"]) - small["dram_bytes"]) <= 1
+    per_ct = (small["dram_bytes"] - bench.BR_KEY_BYTES) / small["ciphertexts"]
+    assert abs(bench.br_traffic(65536) - (bench.BR_KEY_BYTES + 65536 * per_ct)) <= 1
     ntt = tmp_path / "paper_2407_19871_gb300" / "csrc" / "ntt.cuh"
     ntt.write_text(ntt.read_text() + "\n// edited\n")
-    assert bench.br_traffic() is None
+    assert bench.br_traffic(65536) is None
     os.remove(tmp_path / "profiles" / "traffic.json")
-    assert bench.br_traffic() is None
+    assert bench.br_traffic(65536) is None
 
 
 @pytest.mark.slow
