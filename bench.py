@@ -60,6 +60,10 @@ KS_SMEM_BYTES_PER_CT = 1024 * 4 * 632 * 4
 SMEM_BYTES_PER_CLK_SM = 128
 
 
+# Per-device cache of the autotuner's choices (lp_autotune_cached), beside the build outputs.
+TUNING_CACHE = os.environ.get("LOCPIR_TUNING_CACHE", os.path.join(ROOT, "_build", "tuning.json"))
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -163,7 +167,10 @@ def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int =
     ctx.lp_load_bsk_device(bsk)
     ctx.lp_load_ksk_device(ksk)
     del bsk, ksk
-    ctx.split_max = ctx.lp_autotune()   # split/batched blind-rotation crossing on this GPU
+    # launch policy measured on this GPU (or read from the per-device cache written by an earlier run)
+    os.makedirs(os.path.dirname(TUNING_CACHE), exist_ok=True)
+    ctx.tuning = ctx.lp_autotune_cached(TUNING_CACHE)
+    ctx.split_max = ctx.tuning["split_max"]
     A, B = synth.nand_pairs(seed_inputs, count)
     cts = []
     for bits, off in ((A, 0), (B, count)):
@@ -176,13 +183,15 @@ def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int =
     return ctx, p, s_dev, (A, B), cts
 
 
-def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2) -> dict:
+def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2, executor: int = 0) -> dict:
     """LocPIR queries/s on the city-batch shape (l = 32 unsigned, one box, 256-bit service,
     half of the points inside): nq queries scheduled together and captured in a CUDA graph
-    (lp_plan_locpir); one warm-up replay, one timed replay (CUDA events).  Every output is
-    decrypted on the device and compared with the plaintext truth."""
+    (lp_plan_locpir), with the per-level kernels (executor 0) or the persistent executor (1);
+    one warm-up replay, one timed replay (CUDA events).  Every output is decrypted on the
+    device and compared with the plaintext truth."""
     import torch
     from paper_2407_19871_gb300 import locpir
+    ctx.lp_set_executor(executor)
     l, m = 32, 256
     qs = synth.city_batch(seed, nq, l, m)
     per_q = 2 * l + 4 * l + m
@@ -230,10 +239,12 @@ def locpir_throughput(ctx, p, s_dev, nq: int, seed: int = 2) -> dict:
         if bad:
             wrong_queries.append(k)
     plan.lp_plan_destroy()
-    # A bootstrapped gate of this parameter set decides wrongly with probability ~2.4e-7, so a
-    # batch of millions of gates flips about one query's result now and then; the flipped query
-    # is reported (tests/test_gpu_fullsize.py reproduces such a query with the oracle).
+    ctx.lp_set_executor(locpir.LP_EXEC_LEVELS)
+    # The comparators' chained MUX decides wrongly with probability ~1.9e-5 per decision, so a
+    # batch of thousands of queries flips about one query's result now and then; the flipped
+    # query is reported (tests/test_gpu_fullsize.py reproduces such a query with the oracle).
     return {"queries_per_s": nq / sec, "queries": nq, "seconds": sec,
+            "executor": "persistent kernel" if executor else "per-level kernels",
             "blind_rotations_per_s": info["blind_rotations"] / sec, "blind_rotations": info["blind_rotations"],
             "kernels_per_run": info["kernels"], "wrong_bits": wrong, "wrong_queries": wrong_queries[:16],
             "shape": f"city batch: l=32 unsigned, 1 box, m=256, half the points inside (seed {seed}), "
@@ -525,7 +536,9 @@ def _keys_for(n: int):
     ctx = locpir.Context(0, p)
     ctx.lp_load_bsk_device(bsk)
     ctx.lp_load_ksk_device(ksk)
-    ctx.split_max = ctx.lp_autotune()
+    os.makedirs(os.path.dirname(TUNING_CACHE), exist_ok=True)
+    ctx.tuning = ctx.lp_autotune_cached(TUNING_CACHE)
+    ctx.split_max = ctx.tuning["split_max"]
     return ctx, p, s_dev
 
 
@@ -689,6 +702,7 @@ def multibox_uneven(args) -> None:
     zeros, ones = np.flatnonzero(pool_bits == 0), np.flatnonzero(pool_bits == 1)
     total_br = sum(locpir.lp_circuit_info(q.l, 0, len(q.boxes), m, locpir.LP_OR_TREE)["blind_rotations"] for q in qs)
     budget = int(args.multibox_budget_gb * 2**30)
+    ctx.lp_set_executor(locpir.LP_EXEC_PERSISTENT if args.multibox_executor == "persistent" else locpir.LP_EXEC_LEVELS)
     ctx.lp_reset_timing()
     ctx.lp_set_timing(True)
     seconds, waves, wrong_bits, wrong_queries, chunks = 0.0, 0, 0, [], 0
@@ -741,17 +755,19 @@ def multibox_uneven(args) -> None:
         k0 = k1
     br_ms, _ = ctx.lp_kernel_time("br")
     ks_ms, _ = ctx.lp_kernel_time("ks")
+    ex_ms, _ = ctx.lp_kernel_time("exec")
     ctx.lp_set_timing(False)
     hist = {}
     for q in qs:
         hist[q.l] = hist.get(q.l, 0) + 1
-    print(json.dumps({"experiment": "multibox_uneven", "queries": nq, "m": m, "comb": "OR tree",
+    print(json.dumps({"experiment": "multibox_uneven", "executor": args.multibox_executor, "queries": nq, "m": m,
+                      "comb": "OR tree",
                       "boxes_mean": float(np.mean([len(q.boxes) for q in qs])), "widths": hist,
                       "blind_rotations": total_br, "seconds": seconds, "queries_per_s": nq / seconds,
-                      "blind_rotations_per_s": total_br / seconds, "br_kernel_s": br_ms / 1e3, "ks_kernel_s": ks_ms / 1e3,
+                      "blind_rotations_per_s": total_br / seconds, "br_kernel_s": br_ms / 1e3, "ks_kernel_s": ks_ms / 1e3, "exec_kernel_s": ex_ms / 1e3,
                       "chunks": chunks, "waves": waves, "memory_budget_gb": args.multibox_budget_gb,
                       "wrong_bits": wrong_bits, "wrong_queries": len(wrong_queries),
-                      "wrong_query_ids": wrong_queries[:32], "split_max": ctx.split_max}), flush=True)
+                      "wrong_query_ids": wrong_queries[:32], "autotune": ctx.tuning}), flush=True)
     ctx.close()
 
 
@@ -951,6 +967,8 @@ def run_gpu(args) -> None:
     loc = single = None
     if rank == 0 and args.locpir_queries > 0:
         loc = locpir_throughput(ctx, p, s_dev, args.locpir_queries)
+        pers = locpir_throughput(ctx, p, s_dev, args.locpir_queries, executor=locpir.LP_EXEC_PERSISTENT)
+        loc["persistent_executor"] = {k: pers[k] for k in ("queries_per_s", "seconds", "kernels_per_run", "wrong_bits")}
         single = single_query_latency(ctx, p, s_dev)
 
     if rank != 0:
@@ -992,7 +1010,7 @@ def run_gpu(args) -> None:
         "decrypt_errors": wrong,
         "locpir": loc,
         "single_query": single,
-        "autotune": {"split_max": ctx.split_max},
+        "autotune": ctx.tuning,
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -1026,6 +1044,7 @@ def main():
     ap.add_argument("--multibox-queries", type=int, default=1024)
     ap.add_argument("--multibox-budget-gb", type=float, default=96.0)
     ap.add_argument("--multibox-input-gb", type=float, default=32.0)
+    ap.add_argument("--multibox-executor", default="levels", choices=["levels", "persistent"])
     ap.add_argument("--int-peaks", action="store_true",
                     help="integer-pipe throughput microbenchmark (the alu roofline's measured peak)")
     ap.add_argument("--serve-shape", default="uneven", choices=["uneven", "city"])

@@ -188,6 +188,16 @@ typedef struct lp_query {
 } lp_query;
 int lp_locpir_batch(lp_ctx *ctx, const lp_query *q, size_t nq, void *stream);
 
+/* The same queries in memory-budgeted waves: queries are taken in order into a wave while its
+ * circuit's device memory (ciphertext pool and job records: one (n + 1)-word ciphertext per wire
+ * of the levelled circuit, Algorithms 2-5) stays within mem_budget bytes; each wave is scheduled
+ * by bootstrap level as in lp_locpir_batch, and the waves run one after another on the stream.
+ * The pass scratch (at most 131,072 blind rotations: ~0.7 GB) comes on top of the budget.
+ * *waves_out (may be null) receives the number of waves.  LP_ENOMEM if one query alone exceeds
+ * the budget.  Outputs are bit-identical to lp_locpir_batch over the same queries. */
+int lp_locpir_batch_waves(lp_ctx *ctx, const lp_query *q, size_t nq, size_t mem_budget, size_t *waves_out,
+                          void *stream);
+
 /* ---- server-known box bounds (beyond the paper) ------------------------------------------
  * When the server holds the box bounds in the clear, Algorithm 2's second operand is a known
  * bit string: XNOR with a known bit is the point bit or its negation (no bootstrap), and the
@@ -241,14 +251,52 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
 #define LP_KS_TENSOR_INT8 1
 int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
 
-/* lp_autotune: times both NTT blind-rotation kernels on this device (synthetic inputs, levels
- * of 1-4 ciphertexts per SM, CUDA events, about 0.2 s) and sets the widest level the default
- * engine runs split: the largest multiple of the SM count up to which the split kernel is
- * still faster (never below one per SM).  Without it the rule is two ciphertexts per SM,
- * measured on GB300.  *split_max_out (may be NULL) receives the chosen width.  Needs both keys
- * (LP_ENOKEY); uses the context's scratch, so call it while no other work of this context is
- * in flight (not while a server runs).  Results of later calls are bit-identical either way. */
+/* Launch policy of a context, chosen by the autotuner (no counterpart in the paper, whose
+ * gates run one per call on a CPU):
+ *   split_max     the widest level the blind rotation runs on the split kernel (one ciphertext
+ *                 per CTA); 0 = the built-in rule, two ciphertexts per SM;
+ *   tail_split    1: a wider level runs its full batched waves batched and its partial last
+ *                 wave split, when that remainder is at most split_max; 0: all batched;
+ *   ks_slice_max  key switches of at most this many 64-output batches split their input
+ *                 coefficients across CTAs; 0 = the built-in rule (fewer than half the SMs),
+ *                 -1 = never;
+ *   from_cache    (output only) 1 when lp_autotune_cached read the choices from its cache.
+ * Every policy gives the same output bits. */
+#define LP_TUNING_SCHEMA 1
+typedef struct lp_tuning {
+    int split_max, tail_split, ks_slice_max, from_cache;
+} lp_tuning;
+
+/* lp_autotune: measures the policy on this device (synthetic inputs, CUDA events, about 0.5 s):
+ * both NTT blind-rotation kernels at levels of 1-4 ciphertexts per SM (split_max: the largest
+ * multiple of the SM count up to which the split kernel is still faster, never below one per
+ * SM; tail_split when the split kernel beats a batched wave at one per SM), and the key switch
+ * sliced against whole-table CTAs at 1/4 to 1 batch per SM (ks_slice_max: the widest batch
+ * count of the leading run where slicing is faster).  Applies it to the context.
+ * *split_max_out (may be NULL) receives split_max.  Needs both keys (LP_ENOKEY); uses the
+ * context's scratch, so call it while no other work of this context is in flight (not while a
+ * server runs). */
 int lp_autotune(lp_ctx *ctx, int *split_max_out);
+/* lp_autotune_cached: as lp_autotune, but reads the choices from the JSON file cache_path when
+ * it holds an entry for this device (GPU name, SM count, LWE dimension n, LP_TUNING_SCHEMA) and
+ * force is 0; otherwise measures and writes the file (replacing it; cache_path NULL: no file).
+ * *out (may be NULL) receives the applied policy.  LP_EINVAL if the file cannot be written. */
+int lp_autotune_cached(lp_ctx *ctx, const char *cache_path, int force, lp_tuning *out);
+/* Circuit executor of a context (lp_compare_batch, lp_locpir_*, plans; not the server):
+ *   LP_EXEC_LEVELS      per bootstrap level, three kernels (pre-combination, blind rotation, key
+ *                       switch) queued on the stream; plans capture them into one CUDA graph;
+ *   LP_EXEC_PERSISTENT  one persistent kernel (one CTA per SM, cooperative launch) runs every
+ *                       level: its CTAs take the level's gate groups and key-switch batches from
+ *                       device-side counters and meet at grid-wide barriers between phases; a
+ *                       barrier wait that sees no progress for 2 s ends the run with LP_ETIMEOUT.
+ * Both give the same output bits.  LP_EINVAL for another value. */
+#define LP_EXEC_LEVELS 0
+#define LP_EXEC_PERSISTENT 1
+int lp_set_executor(lp_ctx *ctx, int executor);
+
+/* Apply a policy explicitly (e.g. the built-in rules: all fields 0) / read the current one. */
+int lp_set_tuning(lp_ctx *ctx, const lp_tuning *t);
+int lp_get_tuning(const lp_ctx *ctx, lp_tuning *t);
 
 /* lp_circuit_info: the gate statistics of one LocPIR query's circuit (Algorithms 2-5; the
  * comparators of Algorithm 2, validation, bitwiseAND of Algorithm 5, the combine `comb`) as
@@ -361,6 +409,10 @@ int lp_reset_timing(lp_ctx *ctx);
  * a timeout and returns; the next lp_sync reports LP_ETIMEOUT and the context stays usable.
  * Every wait inside the library's kernels uses the same bounded routine (2 s limit). */
 int lp_selftest_wait_timeout(lp_ctx *ctx, uint32_t limit_ms, void *stream);
+/* lp_selftest_exec_timeout: launches the persistent executor on one empty pass with one CTA
+ * leaving at once, so the others' grid-barrier wait runs out after 2 s; synchronous.  The
+ * device error word then holds LP_ETIMEOUT (lp_sync returns it) and the context stays usable. */
+int lp_selftest_exec_timeout(lp_ctx *ctx, void *stream);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,7 @@
 // level.
 #include "common.cuh"
 #include "kernels.h"
+#include "ks_device.cuh"
 #include "ntt.cuh"
 
 namespace lp {
@@ -60,6 +61,7 @@ struct __align__(16) BrSmem {
     uint64_t full_bar[2][BR_RING];
     uint64_t empty_bar[2][BR_RING];
     int abort;
+    int claim;                                           // group handed to this CTA (persistent executor)
 };
 
 struct BrArgs {
@@ -244,8 +246,23 @@ __device__ __forceinline__ uint32_t crt_lift(uint32_t x0, uint32_t x1)
     return r;
 }
 
-// Loop of one compute warp over its CTA's ciphertext groups.
-__device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int warp, int lane, int ngroups)
+// Next group of a CTA that pulls its work from a device-side counter (all threads call it at
+// the same point; the counter hands each group to exactly one CTA).
+__device__ __forceinline__ int claim_group(BrSmem &sm, uint32_t *ctr)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) sm.claim = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    return sm.claim;
+}
+
+// Loop of one compute warp over its CTA's ciphertext groups: groups blockIdx.x, + gridDim.x, ...
+// (Dyn = false), or groups claimed one at a time from *claim (Dyn = true: the persistent
+// executor).  A claimed group's key stream starts when it is claimed; an abort is then decided
+// CTA-wide at the group boundary.  Returns false after an abort.
+template <bool Dyn>
+__device__ __forceinline__ bool compute_warp(BrSmem &sm, const BrArgs &a, int warp, int lane, int ngroups,
+                                             uint32_t *claim = nullptr, uint32_t *progress = nullptr)
 {
     const int slot = warp >> 1;
     const int pi = warp & 1;
@@ -261,11 +278,22 @@ __device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int wa
     pr.n = n;
     pr.pi = pi;
     pr.issued = 0;
-    const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    pr.total = (uint32_t)my_groups * (uint32_t)n * ROWS;
-    if (producer) produce(sm, pr, BR_RING);
-
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    int g;
+    if (Dyn) {
+        pr.total = 0;
+        g = claim_group(sm, claim);
+    } else {
+        const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+        pr.total = (uint32_t)my_groups * (uint32_t)n * ROWS;
+        if (producer) produce(sm, pr, BR_RING);
+        g = blockIdx.x;
+    }
+    bool failed = false;
+    while (g < ngroups) {
+        if (Dyn) {
+            pr.total += (uint32_t)n * ROWS;
+            if (producer) produce(sm, pr, cseq + BR_RING);
+        }
         const int job = g * BR_SLOTS + slot;
         const bool active = job < a.jobs;
         if (pi == 1 && active) {
@@ -303,18 +331,34 @@ __device__ __forceinline__ void compute_warp(BrSmem &sm, const BrArgs &a, int wa
         }
         if (aborted) {
             if (lane == 0 && pi == 1) atomicOr(a.err, DEV_ERR_TIMEOUT);
-            break;
-        }
-        if (pi == 1 && active) {
+        } else if (pi == 1 && active) {
             // Sample extraction: a'_0 = A_0, a'_j = -A_{N-j}, b' = B_0.
             uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
             for (int j = lane; j < RING_N; j += 32)
                 dst[j] = j == 0 ? sm.acc[slot][0][0] : 0u - sm.acc[slot][0][RING_N - j];
             if (lane == 0) dst[RING_N] = sm.acc[slot][1][0];
         }
+        if (Dyn) {
+            if (__syncthreads_or(aborted)) {
+                failed = true;
+                break;
+            }
+            if (threadIdx.x == 0 && progress) atomicAdd(progress, 1u);
+            g = claim_group(sm, claim);
+        } else {
+            if (aborted) {
+                failed = true;
+                break;
+            }
+            g += gridDim.x;
+        }
     }
     // No bulk copy may still be in flight when the CTA exits.
-    if (producer && !drain(sm, pr)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    if (producer && !drain(sm, pr)) {
+        atomicOr(a.err, DEV_ERR_TIMEOUT);
+        failed = true;
+    }
+    return !failed;
 }
 
 __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
@@ -336,7 +380,7 @@ __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
     }
     __syncthreads();
     const int ngroups = (a.jobs + BR_SLOTS - 1) / BR_SLOTS;
-    compute_warp(sm, a, warp, lane, ngroups);
+    compute_warp<false>(sm, a, warp, lane, ngroups);
 }
 
 // ---------------------------------------------------------------------------------
@@ -566,6 +610,198 @@ __global__ void __launch_bounds__(256) bsk_to_ntt_kernel(const uint32_t *bsk, ui
 }
 
 // ---------------------------------------------------------------------------------
+// Persistent circuit executor: one launch runs a whole levelled schedule (every pass of
+// pre-combination + modulus switch, blind rotation + extraction, key switch, then the output
+// copies).  One CTA per SM, all resident (cooperative launch).  Within a phase the CTAs pull
+// their work from device-side counters -- groups of BR_SLOTS blind rotations, key-switch
+// units of one batch (and one coefficient slice) -- so no host step sits between the levels;
+// phases meet at grid-wide barriers whose waits give up after 2 s without progress (a shared
+// progress counter moves with every finished unit), raise a global abort flag and report
+// LP_ETIMEOUT.  Shared memory holds the blind rotation's state or the key switch's, one after
+// the other: each phase initialises its barriers and invalidates them when it ends.
+// ---------------------------------------------------------------------------------
+constexpr uint64_t EXEC_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier over ctl[0] (arrivals) and ctl[1] (generation); ctl[2] counts progress,
+// ctl[3] is the abort flag.  Returns false (CTA-uniformly) when the executor is aborting.
+__device__ bool exec_barrier(uint32_t *ctl, int *err, int *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = ld_acquire_gpu(&ctl[3]) == 0u;
+        const uint32_t gen = ld_acquire_gpu(&ctl[1]);
+        __threadfence();
+        atomicAdd(&ctl[2], 1u);
+        if (atomicAdd(&ctl[0], 1u) == gridDim.x - 1) {
+            atomicExch(&ctl[0], 0u);
+            __threadfence();
+            atomicAdd(&ctl[1], 1u);
+        } else {
+            uint32_t prog = ld_acquire_gpu(&ctl[2]);
+            uint64_t t0 = global_timer_ns();
+            for (uint32_t it = 1; ld_acquire_gpu(&ctl[1]) == gen; ++it) {
+                if ((it & 63u) != 0u) continue;
+                if (ld_acquire_gpu(&ctl[3]) != 0u) break;
+                const uint32_t p = ld_acquire_gpu(&ctl[2]);
+                const uint64_t t = global_timer_ns();
+                if (p != prog) {
+                    prog = p;
+                    t0 = t;
+                } else if (t - t0 > EXEC_WAIT_NS) {
+                    atomicExch(&ctl[3], 1u);
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = ok && ld_acquire_gpu(&ctl[3]) == 0u;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__global__ void __launch_bounds__(BR_THREADS, 1) exec_kernel(ExecArgs x)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BrSmem &bs = *reinterpret_cast<BrSmem *>(smem_raw);
+    KsSmem &ks = *reinterpret_cast<KsSmem *>(smem_raw);
+    __shared__ int s_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = x.n, V = n + 1;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (size_t)gridDim.x * blockDim.x;
+    if (x.selftest_stall && blockIdx.x == 0) return;   // nothing in flight: the wait self-test
+    bool ok = true;
+    for (int p = 0; p < x.npasses && ok; p++) {
+        const ExecPass P = x.passes[p];
+        // Pre-combination + modulus switch of the pass's blind-rotation jobs (every thread).
+        const BrJob *jobs = x.br + P.br_off;
+        for (size_t idx = tid; idx < (size_t)P.br_cnt * V; idx += nthr) {
+            const size_t jb = idx / V;
+            const int w = (int)(idx % V);
+            const BrJob J = jobs[jb];
+            uint32_t v = 0u;
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (J.coef[k] != 0) v += (uint32_t)J.coef[k] * x.pool[(size_t)J.in[k] * V + w];
+            if (w == n) v += J.bconst;
+            x.abar[jb * x.abar_stride + w] = modswitch_2048(v);
+        }
+        if (!(ok = exec_barrier(x.ctl, x.err, &s_flag))) break;
+        // Blind rotation + extraction: groups pulled from the pass's counter.
+        if (P.br_cnt > 0) {
+            for (int i = threadIdx.x; i < 2 * 2 * LANE_TW * 32; i += blockDim.x) (&bs.tw[0][0][0])[i] = x.tw_lane[i];
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < 2; q++)
+                    for (int r = 0; r < BR_RING; r++) {
+                        mbar_init(&bs.full_bar[q][r], 1);
+                        mbar_init(&bs.empty_bar[q][r], BR_SLOTS);
+                    }
+                bs.abort = 0;
+                mbar_fence_init();
+            }
+            __syncthreads();
+            BrArgs a{x.abar, x.ext, x.bsk_hat, x.tw_lane, n, x.abar_stride, (int)P.br_cnt, T_EIGHTH, x.err};
+            const bool good = compute_warp<true>(bs, a, warp, lane, (int)((P.br_cnt + BR_SLOTS - 1) / BR_SLOTS),
+                                                 &x.ctl[4 + 2 * p], &x.ctl[2]);
+            if (__syncthreads_or(!good) && threadIdx.x == 0) atomicExch(&x.ctl[3], 1u);
+            if (threadIdx.x == 0)
+                for (int q = 0; q < 2; q++)
+                    for (int r = 0; r < BR_RING; r++) {
+                        mbar_inval(&bs.full_bar[q][r]);
+                        mbar_inval(&bs.empty_bar[q][r]);
+                    }
+        }
+        if (!(ok = exec_barrier(x.ctl, x.err, &s_flag))) break;
+        // Key switch: units of one batch of KS_CT outputs, split into coefficient slices when the
+        // batches are too few for the SMs (outputs first set to (0, b'), then added into).
+        const KsJob *kj = x.ks + P.ks_off;
+        const size_t nb = ((size_t)P.ks_cnt + KS_CT - 1) / KS_CT;
+        const bool sliced = x.ks_slice_max > 0 ? nb <= (size_t)x.ks_slice_max
+                                               : x.ks_slice_max < 0 ? false : 2 * nb < (size_t)gridDim.x;
+        const int slices = sliced ? ks_slices(nb, gridDim.x) : 1;
+        if (sliced) {
+            ks_init_rows(x.ext, kj, P.ks_cnt, 0, x.pool, n, tid, nthr);
+            if (!(ok = exec_barrier(x.ctl, x.err, &s_flag))) break;
+        }
+        if (P.ks_cnt > 0) {
+            KsProducer pr;
+            ks_setup(ks, pr, x.T, n);
+            __syncthreads();
+            uint32_t cseq = 0;
+            bool good = true;
+            const int nblk = RING_N / KS_ICH;
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_flag = (int)atomicAdd(&x.ctl[5 + 2 * p], 1u);
+                __syncthreads();
+                const size_t u = (size_t)s_flag;
+                if (u >= nb * slices) break;
+                const size_t bt = u / slices;
+                const int sl = (int)(u % slices);
+                const int i_begin = sliced ? (sl * nblk / slices) * KS_ICH : 0;
+                const int i_end = sliced ? ((sl + 1) * nblk / slices) * KS_ICH : RING_N;
+                good = sliced ? ks_unit<true>(ks, pr, cseq, x.ext, kj, P.ks_cnt, 0, x.pool, n, bt, i_begin, i_end)
+                              : ks_unit<false>(ks, pr, cseq, x.ext, kj, P.ks_cnt, 0, x.pool, n, bt, i_begin, i_end);
+                if (!good) break;
+                if (threadIdx.x == 0) atomicAdd(&x.ctl[2], 1u);
+            }
+            if (threadIdx.x == 0 && !ks_drain(ks, pr)) good = false;
+            if (__syncthreads_or(!good) && threadIdx.x == 0) {
+                atomicExch(&x.ctl[3], 1u);
+                atomicOr(x.err, DEV_ERR_TIMEOUT);
+            }
+            if (threadIdx.x == 0)
+                for (int r = 0; r < KS_RING; r++) {
+                    mbar_inval(&ks.full_bar[r]);
+                    mbar_inval(&ks.empty_bar[r]);
+                }
+        }
+        ok = exec_barrier(x.ctl, x.err, &s_flag);
+    }
+    if (!ok) return;
+    // Outputs out of the pool (negated where the output signal is).
+    for (size_t idx = tid; idx < (size_t)x.nout * V; idx += nthr) {
+        const CopyEntry E = x.outc[idx / V];
+        const uint32_t v = E.src[idx % V];
+        E.dst[idx % V] = E.neg ? 0u - v : v;
+    }
+}
+
+size_t exec_smem_bytes() { return sizeof(BrSmem) > sizeof(KsSmem) ? sizeof(BrSmem) : sizeof(KsSmem); }
+
+cudaError_t launch_exec(const ExecArgs &x, int num_sms, cudaStream_t st)
+{
+    const size_t smem = exec_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)num_sms);
+    cfg.blockDim = dim3(BR_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, exec_kernel, x);
+}
+
+// ---------------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------------
 cudaError_t upload_constants(const NttTables &t)
@@ -589,10 +825,32 @@ cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, con
     return cudaGetLastError();
 }
 
+static cudaError_t launch_split(const BrArgs &a, int num_sms, cudaStream_t st)
+{
+    const size_t smem = sizeof(SplitSmem);
+    cudaError_t e = cudaFuncSetAttribute(br_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = a.jobs < num_sms ? a.jobs : num_sms;
+    br_split_kernel<<<grid, SPLIT_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_batched(const BrArgs &a, int num_sms, cudaStream_t st)
+{
+    const size_t smem = sizeof(BrSmem);
+    cudaError_t e = cudaFuncSetAttribute(br_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int groups = (a.jobs + BR_SLOTS - 1) / BR_SLOTS;
+    const int grid = groups < num_sms ? groups : num_sms;
+    br_kernel<<<grid, BR_THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
-                      cudaStream_t st, int variant, int split_max)
+                      cudaStream_t st, int variant, int split_max, int tail_split, int *launched)
 {
+    if (launched) *launched = 0;
     if (jobs <= 0) return cudaSuccess;
     BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
     // Policy (measured on GB300): a split CTA finishes one ciphertext in 4.4-4.8 ms, a batched
@@ -602,20 +860,27 @@ cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, cons
     const int smax = split_max > 0 ? split_max : 2 * num_sms;
     const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= smax);
     if (split) {
-        const size_t smem = sizeof(SplitSmem);
-        cudaError_t e = cudaFuncSetAttribute(br_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int grid = jobs < num_sms ? jobs : num_sms;
-        br_split_kernel<<<grid, SPLIT_THREADS, smem, st>>>(a);
-        return cudaGetLastError();
+        if (launched) *launched = 1;
+        return launch_split(a, num_sms, st);
     }
-    const size_t smem = sizeof(BrSmem);
-    cudaError_t e = cudaFuncSetAttribute(br_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int groups = (jobs + BR_SLOTS - 1) / BR_SLOTS;
-    const int grid = groups < num_sms ? groups : num_sms;
-    br_kernel<<<grid, BR_THREADS, smem, st>>>(a);
-    return cudaGetLastError();
+    // A wider level whose last batched wave would be partial: with tail_split (chosen by the
+    // autotuner), the full waves run batched and the remainder, when it is within the split
+    // crossing, on the split kernel, which finishes it in a fraction of a batched wave.
+    const int wave = BR_SLOTS * num_sms;
+    const int rem = jobs % wave;
+    if (variant == BR_VARIANT_AUTO && tail_split && rem > 0 && rem <= smax && jobs > rem) {
+        BrArgs head = a, tail = a;
+        head.jobs = jobs - rem;
+        tail.jobs = rem;
+        tail.abar = abar + (size_t)head.jobs * abar_stride;
+        tail.ext = ext + (size_t)head.jobs * EXT_STRIDE;
+        cudaError_t e = launch_batched(head, num_sms, st);
+        if (e == cudaSuccess) e = launch_split(tail, num_sms, st);
+        if (launched) *launched = 2;
+        return e;
+    }
+    if (launched) *launched = 1;
+    return launch_batched(a, num_sms, st);
 }
 
 }  // namespace lp

@@ -55,7 +55,9 @@ struct Schedule {
     std::vector<Pass> passes;
     std::vector<CopyEntry> outc;
     std::vector<InputCopy> ins;
-    size_t max_pass = 1, nwires = 0, br_bytes = 0, ks_bytes = 0, out_off = 0, job_bytes = 0;
+    std::vector<ExecPass> xpass;   // the passes for the persistent executor
+    size_t max_pass = 1, nwires = 0, br_bytes = 0, ks_bytes = 0, out_off = 0, xpass_off = 0, ctl_off = 0,
+           job_bytes = 0;
     int zero_w = -1;
 };
 
@@ -90,10 +92,14 @@ static void schedule(const Circuit &C, const std::vector<InputCopy> &ins, const 
     S.ins = ins;
     S.zero_w = C.zero_w;
     S.nwires = C.depth.size();
+    for (const Pass &ps : S.passes)
+        S.xpass.push_back(ExecPass{(uint32_t)ps.br_off, (uint32_t)ps.br_cnt, (uint32_t)ps.ks_off, (uint32_t)ps.ks_cnt});
     S.br_bytes = S.br.size() * sizeof(BrJob);
     S.ks_bytes = S.ks.size() * sizeof(KsJob);
     S.out_off = (S.br_bytes + S.ks_bytes + 255) & ~(size_t)255;
-    S.job_bytes = S.out_off + S.outc.size() * sizeof(CopyEntry) + 256;
+    S.xpass_off = (S.out_off + S.outc.size() * sizeof(CopyEntry) + 255) & ~(size_t)255;
+    S.ctl_off = (S.xpass_off + S.xpass.size() * sizeof(ExecPass) + 255) & ~(size_t)255;
+    S.job_bytes = S.ctl_off + exec_ctl_words((int)S.xpass.size()) * sizeof(uint32_t) + 256;
 }
 
 // Buffers a schedule runs on.
@@ -115,6 +121,9 @@ static cudaError_t upload_schedule(Schedule &S, const RunBufs &B, cudaStream_t s
         e = cudaMemcpyAsync(B.jobs + S.br_bytes, S.ks.data(), S.ks_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !S.outc.empty())
         e = cudaMemcpyAsync(B.jobs + S.out_off, S.outc.data(), S.outc.size() * sizeof(CopyEntry),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !S.xpass.empty())
+        e = cudaMemcpyAsync(B.jobs + S.xpass_off, S.xpass.data(), S.xpass.size() * sizeof(ExecPass),
                             cudaMemcpyHostToDevice, st);
     return e;
 }
@@ -139,23 +148,42 @@ static int enqueue_schedule(lp_ctx *c, const Schedule &S, const RunBufs &B, cuda
     const BrJob *dbr = reinterpret_cast<const BrJob *>(B.jobs);
     const KsJob *dks = reinterpret_cast<const KsJob *>(B.jobs + S.br_bytes);
     int *err = static_cast<int *>(c->err.ptr);
+    if (c->executor == LP_EXEC_PERSISTENT) {
+        // One persistent launch runs every pass and the output copies; its control words start
+        // at zero on every run (a memset node when captured into a plan's graph).
+        uint32_t *ctl = reinterpret_cast<uint32_t *>(B.jobs + S.ctl_off);
+        e = cudaMemsetAsync(ctl, 0, exec_ctl_words((int)S.xpass.size()) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "executor control words");
+        ExecArgs x{reinterpret_cast<const ExecPass *>(B.jobs + S.xpass_off), (int)S.xpass.size(), dbr, dks,
+                   reinterpret_cast<const CopyEntry *>(B.jobs + S.out_off), (uint32_t)S.outc.size(), B.pool, B.abar,
+                   abar_stride(c), B.ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                   static_cast<const uint2 *>(c->tw_lane.ptr), static_cast<const uint32_t *>(c->ksk.ptr), n,
+                   c->ks_slice_max, err, ctl, 0};
+        cudaEvent_t ev0 = nullptr;
+        if (timed) timer_begin(c, "exec", st, &ev0);
+        e = launch_exec(x, c->num_sms, st);
+        if (timed) timer_end(c, "exec", st, ev0);
+        c->launches++;
+        return e == cudaSuccess ? LP_OK : cuda_fail(e, "persistent executor launch");
+    }
     for (const Pass &ps : S.passes) {
         e = launch_precomb_indexed(dbr + ps.br_off, ps.br_cnt, B.pool, n, B.abar, abar_stride(c), c->num_sms, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
         cudaEvent_t ev0 = nullptr;
         if (timed) timer_begin(c, "br", st, &ev0);
+        int launched = 0;
         e = launch_br(B.abar, abar_stride(c), B.ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
                       static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)ps.br_cnt, T_EIGHTH, err, c->num_sms, st,
-                      BR_VARIANT_AUTO, c->br_split_max);
+                      BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, &launched);
         if (timed) timer_end(c, "br", st, ev0);
-        c->launches++;
+        c->launches += launched;
         if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
         if (timed) timer_begin(c, "ks", st, &ev0);
         e = launch_ks(B.ext, dks + ps.ks_off, ps.ks_cnt, 0, B.pool, static_cast<const uint32_t *>(c->ksk.ptr), n, err,
-                      c->num_sms, st);
+                      c->num_sms, st, c->ks_slice_max, &launched);
         if (timed) timer_end(c, "ks", st, ev0);
-        c->launches++;
+        c->launches += launched;
         if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
     }
     if (!S.outc.empty()) {
@@ -263,6 +291,70 @@ extern "C" int lp_locpir_batch(lp_ctx *c, const lp_query *q, size_t nq, void *st
         for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{S[j], Q.out_service + (size_t)j * W});
     }
     return execute(c, C, ins, outs, static_cast<cudaStream_t>(stream));
+}
+
+// Device bytes a built circuit needs while it runs: its ciphertext pool and its job records
+// (the pass scratch is bounded separately by the largest pass).
+static size_t circuit_bytes(const Circuit &C, size_t outputs, int n)
+{
+    const size_t W = (size_t)n + 1;
+    size_t br = 0;
+    for (const Node &nd : C.nodes) br += nd.op == LP_MUX ? 2 : 1;
+    return C.depth.size() * W * 4 + br * sizeof(BrJob) + C.nodes.size() * sizeof(KsJob) + outputs * sizeof(CopyEntry);
+}
+
+extern "C" int lp_locpir_batch_waves(lp_ctx *c, const lp_query *q, size_t nq, size_t mem_budget, size_t *waves_out,
+                                     void *stream)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (waves_out) *waves_out = 0;
+    if (nq == 0) return LP_OK;
+    if (!q) return fail(LP_EINVAL, "null query array");
+    for (size_t i = 0; i < nq; i++)
+        if ((rc = check_query(q[i]))) return rc;
+    const int n = c->params.n;
+    const size_t W = (size_t)n + 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    size_t next = 0, waves = 0;
+    while (next < nq) {
+        // Grow the wave query by query; a query that takes it over the budget is taken back
+        // (the builder only appends, so truncating restores the circuit) and opens the next wave.
+        Circuit C;
+        std::vector<InputCopy> ins;
+        std::vector<OutputCopy> outs;
+        size_t first = next;
+        while (next < nq) {
+            const size_t nw = C.depth.size(), nn = C.nodes.size(), ni = ins.size(), no = outs.size();
+            const int zw = C.zero_w;
+            const lp_query &Q = q[next];
+            const int x = C.inputs(Q.l), y = C.inputs(Q.l);
+            const int bx = C.inputs(4 * Q.l * Q.n_boxes);
+            const int sv = C.inputs(Q.m * Q.n_boxes);
+            ins.push_back(InputCopy{x, Q.x, Q.l});
+            ins.push_back(InputCopy{y, Q.y, Q.l});
+            ins.push_back(InputCopy{bx, Q.boxes, 4 * Q.l * Q.n_boxes});
+            ins.push_back(InputCopy{sv, Q.services, Q.m * Q.n_boxes});
+            std::vector<Sig> S = build_locpir(C, Q.l, Q.is_signed != 0, x, y, Q.n_boxes, bx, Q.m, sv, Q.comb);
+            for (int j = 0; j < Q.m; j++) outs.push_back(OutputCopy{S[j], Q.out_service + (size_t)j * W});
+            if (circuit_bytes(C, outs.size(), n) > mem_budget) {
+                if (next == first)
+                    return fail(LP_ENOMEM, "query %zu alone needs %zu bytes, above the memory budget of %zu", next,
+                                circuit_bytes(C, outs.size(), n), mem_budget);
+                C.depth.resize(nw);
+                C.nodes.resize(nn);
+                C.zero_w = zw;
+                ins.resize(ni);
+                outs.resize(no);
+                break;
+            }
+            next++;
+        }
+        if ((rc = execute(c, C, ins, outs, st))) return rc;
+        waves++;
+    }
+    if (waves_out) *waves_out = waves;
+    return LP_OK;
 }
 
 extern "C" int lp_locpir_query(lp_ctx *c, int l, int is_signed, const uint32_t *x, const uint32_t *y, int n_boxes,

@@ -238,12 +238,6 @@ inline std::vector<std::vector<int>> levels_of(const Circuit &C)
 }
 
 // One ciphertext copied entry (pool <-> caller), optionally negated.
-struct CopyEntry {
-    const uint32_t *src;
-    uint32_t *dst;
-    int32_t neg;
-    int32_t pad;
-};
 cudaError_t launch_copy_entries(const CopyEntry *e, size_t cnt, int n, int num_sms, cudaStream_t st);
 
 // Argument checks of one LocPIR query (LP_EINVAL with a message).

@@ -38,6 +38,9 @@ constexpr int LANE_TW = 31;
 
 __device__ __forceinline__ uint32_t umin_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
+// Modulus switch of a torus32 word to Z_2N (2N = 2048), rounding half up: ((x + 2^20) mod 2^32) >> 21.
+__device__ __forceinline__ uint16_t modswitch_2048(uint32_t x) { return (uint16_t)((x + (1u << 20)) >> 21); }
+
 // ---------------------------------------------------------------------------------
 // PTX wrappers: mbarrier, bulk async copy, timers.
 // ---------------------------------------------------------------------------------

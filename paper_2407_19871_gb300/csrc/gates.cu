@@ -11,7 +11,6 @@ namespace lp {
 // (LocPIR Section 2.2, EvalGate: HomAND uses (0, -1/8) + c1 + c2), then rounds every
 // coefficient to Z_2N: abar = ((x + 2^20) mod 2^32) >> 21 (half up).
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ uint16_t modswitch_2048(uint32_t x) { return (uint16_t)((x + (1u << 20)) >> 21); }
 
 __device__ __forceinline__ void gate_coefs(int op, int half, uint32_t &cst, int &ca, int &cb, int &cc)
 {

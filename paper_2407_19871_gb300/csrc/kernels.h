@@ -22,7 +22,50 @@ struct KsJob {
     int32_t out;
 };
 
+// One copy of a ciphertext out of the circuit pool, negated when neg != 0.
+struct CopyEntry {
+    const uint32_t *src;
+    uint32_t *dst;
+    int32_t neg;
+    int32_t pad;
+};
+
+// Persistent circuit executor (blind_rotate.cu): one launch runs every pass of a levelled
+// schedule.  A pass is the pre-combination + blind rotation of br_cnt jobs from br_off and the
+// key switch of ks_cnt jobs from ks_off.
+struct ExecPass {
+    uint32_t br_off, br_cnt, ks_off, ks_cnt;
+};
+struct ExecArgs {
+    const ExecPass *passes;
+    int npasses;
+    const BrJob *br;
+    const KsJob *ks;
+    const CopyEntry *outc;
+    uint32_t nout;
+    uint32_t *pool;
+    uint16_t *abar;
+    int abar_stride;
+    uint32_t *ext;
+    const uint32_t *bsk_hat;
+    const uint2 *tw_lane;
+    const uint32_t *T;
+    int n;
+    int ks_slice_max;
+    int *err;
+    uint32_t *ctl;   // exec_ctl_words(npasses) words, zero before the launch
+    int selftest_stall;   // self-test only: CTA 0 leaves before the first barrier, so the others' wait runs out
+};
+// Control words: barrier count, barrier generation, progress, abort flag, then per pass the
+// blind-rotation and key-switch work counters.
+__host__ __device__ __forceinline__ size_t exec_ctl_words(int npasses) { return 4 + 2 * (size_t)npasses; }
+size_t exec_smem_bytes();
+// Cooperative launch over one CTA per SM (every CTA must be resident: the phases meet at
+// grid-wide barriers whose waits give up, with LP_ETIMEOUT, after 2 s without progress).
+cudaError_t launch_exec(const ExecArgs &x, int num_sms, cudaStream_t st);
+
 size_t br_smem_bytes();
+size_t ks_smem_bytes();
 size_t br_split_smem_bytes();
 // Blind-rotation kernel choice: AUTO runs levels of at most split_max ciphertexts split
 // (br_split_kernel, one ciphertext per CTA over 12 warps) and larger ones batched
@@ -32,9 +75,12 @@ size_t br_split_smem_bytes();
 constexpr int BR_VARIANT_AUTO = 0;
 constexpr int BR_VARIANT_BATCHED = 1;
 constexpr int BR_VARIANT_SPLIT = 2;
+// tail_split: with AUTO, a level wider than split_max runs its full batched waves batched and
+// the remainder split when the remainder is at most split_max.  *launched (may be null)
+// receives the number of kernels launched.
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms, cudaStream_t st,
-                      int variant = BR_VARIANT_AUTO, int split_max = 0);
+                      int variant = BR_VARIANT_AUTO, int split_max = 0, int tail_split = 0, int *launched = nullptr);
 cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane, uint32_t scale0,
                               uint32_t scale1, int num_sms, cudaStream_t st);
 cudaError_t launch_precomb_dense(int op, const uint32_t *a, const uint32_t *b, const uint32_t *c, int n,
@@ -43,9 +89,15 @@ cudaError_t launch_modswitch(const uint32_t *lwe, int n, size_t jobs, uint16_t *
                              cudaStream_t st);
 cudaError_t launch_precomb_indexed(const BrJob *jobs, size_t njobs, const uint32_t *pool, int n, uint16_t *abar,
                                    int abar_stride, int num_sms, cudaStream_t st);
-// Key switch from the digit-pair table T (built by launch_ks_table at key load).
+// Key switch from the digit-pair table T (built by launch_ks_table at key load).  Batches of
+// KS_CT outputs; when there are at most slice_max batches (0: fewer than half the SMs), the
+// input coefficients are split across CTAs (see keyswitch.cu).  *launched as for launch_br.
 cudaError_t launch_ks(const uint32_t *ext, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out,
-                      const uint32_t *T, int n, int *err, int num_sms, cudaStream_t st);
+                      const uint32_t *T, int n, int *err, int num_sms, cudaStream_t st, int slice_max = 0,
+                      int *launched = nullptr);
+// Sliced (1) or whole-table (0) key switch regardless of the batch count (autotuner).
+cudaError_t launch_ks_forced(const uint32_t *ext, size_t njobs, uint32_t *out, const uint32_t *T, int n, int *err,
+                             int num_sms, cudaStream_t st, int sliced);
 cudaError_t launch_ks_table(const uint32_t *ksk, uint32_t *T, int n, int num_sms, cudaStream_t st);
 // Words per key-switch table row and per output ciphertext buffer row: n + 1 rounded up to 4.
 __host__ __device__ __forceinline__ int ks_row_words(int n) { return ((n + 1) + 3) & ~3; }

@@ -424,12 +424,14 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
     const int variant = c->br_engine == LP_BR_NTT_BATCHED ? BR_VARIANT_BATCHED
                         : c->br_engine == LP_BR_NTT_SPLIT ? BR_VARIANT_SPLIT
                                                           : BR_VARIANT_AUTO;
+    int launched = 0;
     cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
-                              static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max);
+                              static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max,
+                              c->br_tail_split, &launched);
     timer_end(c, "br", st, ev0);
-    c->launches++;
+    c->launches += launched;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
     return LP_OK;
 }
@@ -443,11 +445,12 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
         timer_end(c, "ks", st, ev0);
         return rc;
     }
+    int launched = 0;
     cudaError_t e = launch_ks(static_cast<const uint32_t *>(c->ext.ptr), jobs, njobs, dense_mux, out,
                               static_cast<const uint32_t *>(c->ksk.ptr), c->params.n,
-                              static_cast<int *>(c->err.ptr), c->num_sms, st);
+                              static_cast<int *>(c->err.ptr), c->num_sms, st, c->ks_slice_max, &launched);
     timer_end(c, "ks", st, ev0);
-    c->launches++;
+    c->launches += launched;
     if (e != cudaSuccess) return cuda_fail(e, "key switch launch");
     return LP_OK;
 }
@@ -471,16 +474,39 @@ extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
     return LP_OK;
 }
 
-extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
+// Median of three timed launches (after one untimed) of fn on the default stream, in ms.
+template <class F>
+static cudaError_t time_median(F fn, float *ms)
 {
-    if (!c) return fail(LP_EINVAL, "null context");
-    if (!c->have_bsk || !c->have_ksk) return fail(LP_ENOKEY, "load the bootstrapping and key-switching keys first");
-    cudaSetDevice(c->device);
-    const int S = c->num_sms, maxw = 4 * S, stride = abar_stride(c);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t[3] = {};
+    cudaError_t e = fn();
+    for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, 0);
+        e = fn();
+        cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) cudaEventElapsedTime(&t[rep], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return e;
+}
+
+// Measure the launch policy on this device: the blind rotation's split/batched crossing (which
+// also decides whether a wider level's partial last wave runs split) and the key switch's
+// slicing crossing.  Synthetic inputs; every choice gives the same bits.
+static int measure_tuning(lp_ctx *c, lp_tuning *t)
+{
+    const int S = c->num_sms, maxw = 4 * S, stride = abar_stride(c), n = c->params.n;
     int rc = ensure_scratch(c, (size_t)maxw);
     if (rc) return rc;
-    // Synthetic mod-switched inputs: every coefficient in [0, 2N) from a fixed LCG, so that no
-    // CMux step is skipped.
+    // Mod-switched inputs: every coefficient in [0, 2N) from a fixed LCG, so that no CMux step is
+    // skipped.
     std::vector<uint16_t> h((size_t)maxw * stride);
     uint32_t x = 12345u;
     for (uint16_t &v : h) {
@@ -489,34 +515,196 @@ extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
     }
     cudaError_t e = cudaMemcpy(c->abar.ptr, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "autotune inputs");
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float t[5][2] = {};
-    for (int k = 1; k <= 4 && e == cudaSuccess; k++) {
+    float tb[5][2] = {};
+    for (int k = 1; k <= 4 && e == cudaSuccess; k++)
         for (int v = 0; v < 2 && e == cudaSuccess; v++) {
             const int variant = v ? BR_VARIANT_SPLIT : BR_VARIANT_BATCHED;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // warm-up, then timed
-                cudaEventRecord(e0, 0);
-                e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), stride, static_cast<uint32_t *>(c->ext.ptr),
-                              static_cast<const uint32_t *>(c->bsk_hat.ptr), static_cast<const uint2 *>(c->tw_lane.ptr),
-                              c->params.n, k * S, T_EIGHTH, static_cast<int *>(c->err.ptr), S, 0, variant);
-                c->launches++;
-                cudaEventRecord(e1, 0);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess) cudaEventElapsedTime(&t[k][v], e0, e1);
-            }
+            e = time_median(
+                [&] {
+                    c->launches++;
+                    return launch_br(static_cast<const uint16_t *>(c->abar.ptr), stride,
+                                     static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                                     static_cast<const uint2 *>(c->tw_lane.ptr), n, k * S, T_EIGHTH,
+                                     static_cast<int *>(c->err.ptr), S, 0, variant);
+                },
+                &tb[k][v]);
         }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess) return cuda_fail(e, "autotune");
-    if ((rc = ctx_check_err(c))) return rc;
-    // Levels below one wave always favour the split kernel; widen while it stays faster.
+    if (e != cudaSuccess) return cuda_fail(e, "autotune blind rotation");
+    // Levels below one wave always favour the split kernel; widen while it stays faster.  The
+    // same crossing bounds the partial last wave that a wider level may run split.
     int best = S;
-    for (int k = 2; k <= 4 && t[k][1] < t[k][0]; k++) best = k * S;
-    c->br_split_max = best;
-    if (split_max_out) *split_max_out = best;
+    for (int k = 2; k <= 4 && tb[k][1] < tb[k][0]; k++) best = k * S;
+    t->split_max = best;
+    t->tail_split = tb[1][1] < tb[1][0] ? 1 : 0;
+    // Key switch: sliced against whole-table CTAs at 1/4 .. 1 batch per SM (64 outputs each),
+    // on the extracted samples the blind rotations just wrote.
+    DevBuf out;
+    const int kmax = 4;
+    rc = ensure_buf(out, (size_t)S * 64 * (n + 1) * sizeof(uint32_t), "autotune key-switch output");
+    if (rc) return rc;
+    if ((size_t)S * 64 > (size_t)maxw) rc = ensure_scratch(c, (size_t)S * 64);
+    if (rc) {
+        free_buf(out);
+        return rc;
+    }
+    int slice_max = 0;
+    for (int k = 1; k <= kmax && e == cudaSuccess; k++) {
+        const size_t nb = (size_t)S * k / kmax, jobs = nb * 64;
+        float ts[2] = {};
+        for (int v = 0; v < 2 && e == cudaSuccess; v++)
+            e = time_median(
+                [&] {
+                    c->launches++;
+                    return launch_ks_forced(static_cast<const uint32_t *>(c->ext.ptr), jobs,
+                                            static_cast<uint32_t *>(out.ptr), static_cast<const uint32_t *>(c->ksk.ptr),
+                                            n, static_cast<int *>(c->err.ptr), S, 0, v);
+                },
+                &ts[v]);
+        if (e == cudaSuccess && ts[1] < ts[0] && (size_t)slice_max == nb - (size_t)S / kmax) slice_max = (int)nb;
+    }
+    free_buf(out);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune key switch");
+    t->ks_slice_max = slice_max > 0 ? slice_max : -1;   // -1: never slice
+    return ctx_check_err(c);
+}
+
+static void apply_tuning(lp_ctx *c, const lp_tuning &t)
+{
+    c->br_split_max = t.split_max;
+    c->br_tail_split = t.tail_split;
+    c->ks_slice_max = t.ks_slice_max;
+}
+
+extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (!c->have_bsk || !c->have_ksk) return fail(LP_ENOKEY, "load the bootstrapping and key-switching keys first");
+    cudaSetDevice(c->device);
+    lp_tuning t{};
+    int rc = measure_tuning(c, &t);
+    if (rc) return rc;
+    apply_tuning(c, t);
+    if (split_max_out) *split_max_out = t.split_max;
+    return LP_OK;
+}
+
+// The cache key: what the measured choices depend on.
+static std::string tuning_key(const lp_ctx *c)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c->device);
+    char buf[320];
+    snprintf(buf, sizeof buf, "%s|sms=%d|n=%d|schema=%d", prop.name, c->num_sms, c->params.n, LP_TUNING_SCHEMA);
+    return buf;
+}
+
+// A flat JSON object of one string field and integer fields, written and read by this library.
+static bool read_tuning(const char *path, const std::string &key, lp_tuning *t)
+{
+    FILE *f = fopen(path, "rb");
+    if (!f) return false;
+    std::string txt;
+    char chunk[4096];
+    size_t got;
+    while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) txt.append(chunk, got);
+    fclose(f);
+    auto field = [&](const char *name, std::string *str, long *num) -> bool {
+        const std::string pat = std::string("\"") + name + "\":";
+        size_t p = txt.find(pat);
+        if (p == std::string::npos) return false;
+        p += pat.size();
+        while (p < txt.size() && txt[p] == ' ') p++;
+        if (str) {
+            if (p >= txt.size() || txt[p] != '"') return false;
+            const size_t q = txt.find('"', p + 1);
+            if (q == std::string::npos) return false;
+            *str = txt.substr(p + 1, q - p - 1);
+            return true;
+        }
+        char *end = nullptr;
+        *num = strtol(txt.c_str() + p, &end, 10);
+        return end != txt.c_str() + p;
+    };
+    std::string k;
+    long sm = 0, ts = 0, ks = 0;
+    if (!field("key", &k, nullptr) || k != key) return false;
+    if (!field("split_max", nullptr, &sm) || !field("tail_split", nullptr, &ts) || !field("ks_slice_max", nullptr, &ks))
+        return false;
+    if (sm < 1 || sm > 1 << 20 || (ts != 0 && ts != 1) || ks < -1 || ks > 1 << 20) return false;
+    t->split_max = (int)sm;
+    t->tail_split = (int)ts;
+    t->ks_slice_max = (int)ks;
+    return true;
+}
+
+static int write_tuning(const char *path, const std::string &key, const lp_tuning &t)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(LP_EINVAL, "cannot write the tuning cache %s", tmp.c_str());
+    std::string k;
+    for (char ch : key) k += (ch == '"' || ch == '\\') ? '_' : ch;
+    fprintf(f, "{\"key\": \"%s\", \"split_max\": %d, \"tail_split\": %d, \"ks_slice_max\": %d}\n", k.c_str(),
+            t.split_max, t.tail_split, t.ks_slice_max);
+    const bool ok = fclose(f) == 0;
+    if (!ok || rename(tmp.c_str(), path) != 0) return fail(LP_EINVAL, "cannot write the tuning cache %s", path);
+    return LP_OK;
+}
+
+extern "C" int lp_autotune_cached(lp_ctx *c, const char *cache_path, int force, lp_tuning *out)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (!c->have_bsk || !c->have_ksk) return fail(LP_ENOKEY, "load the bootstrapping and key-switching keys first");
+    cudaSetDevice(c->device);
+    std::string key = tuning_key(c);
+    for (char &ch : key)
+        if (ch == '"' || ch == '\\') ch = '_';
+    lp_tuning t{};
+    if (cache_path && !force && read_tuning(cache_path, key, &t)) {
+        t.from_cache = 1;
+    } else {
+        int rc = measure_tuning(c, &t);
+        if (rc) return rc;
+        t.from_cache = 0;
+        if (cache_path && (rc = write_tuning(cache_path, key, t))) return rc;
+    }
+    apply_tuning(c, t);
+    if (out) *out = t;
+    return LP_OK;
+}
+
+extern "C" int lp_set_executor(lp_ctx *c, int executor)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (executor != LP_EXEC_LEVELS && executor != LP_EXEC_PERSISTENT)
+        return fail(LP_EINVAL, "unknown executor %d", executor);
+    if (executor == LP_EXEC_PERSISTENT) {
+        cudaSetDevice(c->device);
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+        if (!coop) return fail(LP_EINVAL, "device %d does not support cooperative launches", c->device);
+    }
+    c->executor = executor;
+    return LP_OK;
+}
+
+extern "C" int lp_set_tuning(lp_ctx *c, const lp_tuning *t)
+{
+    if (!c || !t) return fail(LP_EINVAL, "null argument");
+    if (t->split_max < 0 || (t->tail_split != 0 && t->tail_split != 1) || t->ks_slice_max < -1)
+        return fail(LP_EINVAL, "invalid tuning (split_max %d, tail_split %d, ks_slice_max %d)", t->split_max,
+                    t->tail_split, t->ks_slice_max);
+    apply_tuning(c, *t);
+    return LP_OK;
+}
+
+extern "C" int lp_get_tuning(const lp_ctx *c, lp_tuning *t)
+{
+    if (!c || !t) return fail(LP_EINVAL, "null argument");
+    *t = lp_tuning{};
+    t->split_max = c->br_split_max;
+    t->tail_split = c->br_tail_split;
+    t->ks_slice_max = c->ks_slice_max;
     return LP_OK;
 }
 
@@ -722,6 +910,35 @@ extern "C" int lp_preprocess_services(int n, const uint32_t *zero, const uint8_t
     if (!zero || !bits || !out) return fail(LP_EINVAL, "null pointer");
     cudaError_t e = launch_preprocess(n, zero, bits, out, count, device_sms(), static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? LP_OK : cuda_fail(e, "preprocess launch");
+}
+
+extern "C" int lp_selftest_exec_timeout(lp_ctx *c, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    cudaSetDevice(c->device);
+    // One empty pass; CTA 0 leaves at once, so the other CTAs' first grid barrier sees no
+    // progress and gives up after 2 s, raising LP_ETIMEOUT.  No copy is in flight at any point.
+    DevBuf ctl, pass;
+    int rc = ensure_buf(ctl, exec_ctl_words(1) * sizeof(uint32_t), "self-test control words");
+    if (!rc) rc = ensure_buf(pass, sizeof(ExecPass), "self-test pass");
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ctl.ptr, 0, exec_ctl_words(1) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pass.ptr, 0, sizeof(ExecPass), st);
+    ExecArgs x{};
+    x.passes = static_cast<const ExecPass *>(pass.ptr);
+    x.npasses = 1;
+    x.n = c->params.n;
+    x.abar_stride = abar_stride(c);
+    x.err = static_cast<int *>(c->err.ptr);
+    x.ctl = static_cast<uint32_t *>(ctl.ptr);
+    x.selftest_stall = 1;
+    if (e == cudaSuccess) e = launch_exec(x, c->num_sms, st);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_buf(ctl);
+    free_buf(pass);
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "executor self-test");
 }
 
 extern "C" int lp_selftest_wait_timeout(lp_ctx *c, uint32_t limit_ms, void *stream)

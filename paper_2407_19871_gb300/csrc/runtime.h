@@ -44,6 +44,9 @@ struct lp_ctx {
     // Alternative tensor-core engines (tensor_engine.cu) and their state.
     int br_engine = LP_BR_NTT, ks_engine = LP_KS_TABLE;
     int br_split_max = 0;           // widest level run split (0: the default rule; lp_autotune)
+    int br_tail_split = 0;          // a wider level's partial last wave runs split (lp_autotune)
+    int ks_slice_max = 0;           // key switches of at most this many batches run sliced (0: rule)
+    int executor = LP_EXEC_LEVELS;  // circuits: per-level kernels or the persistent executor
     void *blas = nullptr;           // cuBLAS handle, created on first use
     lp::DevBuf bsk_coef;            // coefficient-domain BSK (Toeplitz engine)
     lp::DevBuf tc_T, tc_D, tc_C, tc_acc, ks_A, ks_H, ks_C, ks_aux;

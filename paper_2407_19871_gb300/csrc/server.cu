@@ -226,16 +226,17 @@ static int tick(Server &S)
     for (const Pass &p : passes) {
         e = launch_precomb_indexed(dbr + p.br_off, p.br_cnt, pool, n, static_cast<uint16_t *>(S.abar.ptr),
                                    abar_stride(c), c->num_sms, S.st);
+        int lb = 0, lk = 0;
         if (e == cudaSuccess)
             e = launch_br(static_cast<const uint16_t *>(S.abar.ptr), abar_stride(c), static_cast<uint32_t *>(S.ext.ptr),
                           static_cast<const uint32_t *>(c->bsk_hat.ptr), static_cast<const uint2 *>(c->tw_lane.ptr), n,
                           (int)p.br_cnt, T_EIGHTH, static_cast<int *>(c->err.ptr), c->num_sms, S.st,
-                          BR_VARIANT_AUTO, c->br_split_max);
+                          BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, &lb);
         if (e == cudaSuccess)
             e = launch_ks(static_cast<const uint32_t *>(S.ext.ptr), dks + p.ks_off, p.ks_cnt, 0, pool,
                           static_cast<const uint32_t *>(c->ksk.ptr), n, static_cast<int *>(c->err.ptr), c->num_sms,
-                          S.st);
-        c->launches += 3;
+                          S.st, c->ks_slice_max, &lk);
+        c->launches += 1 + lb + lk;
         if (e != cudaSuccess) return cuda_fail(e, "server: pass launch");
         tick_bootstraps += p.br_cnt;
     }

@@ -26,18 +26,21 @@ EXPORTS = [
     "lp_params_default", "lp_create", "lp_destroy", "lp_sync", "lp_strerror", "lp_last_error",
     "lp_load_bsk", "lp_load_bsk_device", "lp_load_ksk", "lp_load_ksk_device",
     "lp_gate_batch", "lp_gate_batch_host", "lp_gate_batch_noalloc", "lp_bootstrap_extract", "lp_key_switch",
-    "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch", "lp_compare_known_batch", "lp_locpir_known_batch",
+    "lp_compare_batch", "lp_locpir_query", "lp_locpir_batch", "lp_locpir_batch_waves", "lp_compare_known_batch",
+    "lp_locpir_known_batch",
     "lp_client_lwe_encrypt", "lp_client_lwe_phase", "lp_client_keygen_bsk", "lp_client_keygen_ksk",
     "lp_launch_count", "lp_set_timing", "lp_kernel_time", "lp_reset_timing",
     "lp_preprocess_services", "lp_selftest_wait_timeout",
     "lp_server_start", "lp_server_submit", "lp_server_submit_known", "lp_server_poll", "lp_server_wait", "lp_server_stats", "lp_server_stop",
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
-    "lp_plan_locpir_known", "lp_circuit_info",
+    "lp_plan_locpir_known", "lp_circuit_info", "lp_autotune_cached", "lp_set_tuning", "lp_get_tuning",
+    "lp_set_executor", "lp_selftest_exec_timeout",
 ]
 LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
 LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
+LP_EXEC_LEVELS, LP_EXEC_PERSISTENT = 0, 1
 
 
 class lp_params(ctypes.Structure):
@@ -66,6 +69,10 @@ class lp_stats(ctypes.Structure):
 class lp_circuit_stats(ctypes.Structure):
     _fields_ = [("gates_by_op", ctypes.c_uint64 * 8)] + \
                [(k, ctypes.c_uint64) for k in ("blind_rotations", "key_switches", "levels", "widest_level", "wires")]
+
+
+class lp_tuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("split_max", "tail_split", "ks_slice_max", "from_cache")]
 
 
 class LocpirError(RuntimeError):
@@ -105,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "lp_compare_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
             "lp_locpir_query": (i, [vp, i, i, vp, vp, i, vp, i, vp, i, vp, vp]),
             "lp_locpir_batch": (i, [vp, ctypes.POINTER(lp_query), sz, vp]),
+            "lp_locpir_batch_waves": (i, [vp, ctypes.POINTER(lp_query), sz, sz, ctypes.POINTER(sz), vp]),
             "lp_compare_known_batch": (i, [vp, i, i, i, vp, vp, vp, sz, vp]),
             "lp_locpir_known_batch": (i, [vp, ctypes.POINTER(lp_query_known), sz, vp]),
             "lp_client_lwe_encrypt": (i, [i, vp, vp, vp, vp, vp, sz, vp]),
@@ -137,6 +145,11 @@ def lib() -> ctypes.CDLL:
             "lp_plan_destroy": (i, [vp]),
             "lp_set_engines": (i, [vp, i, i]),
             "lp_autotune": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
+            "lp_autotune_cached": (i, [vp, ctypes.c_char_p, i, ctypes.POINTER(lp_tuning)]),
+            "lp_set_tuning": (i, [vp, ctypes.POINTER(lp_tuning)]),
+            "lp_set_executor": (i, [vp, i]),
+            "lp_selftest_exec_timeout": (i, [vp, vp]),
+            "lp_get_tuning": (i, [vp, ctypes.POINTER(lp_tuning)]),
             "lp_circuit_info": (i, [i, i, i, i, i, vp, ctypes.POINTER(lp_circuit_stats)]),
         }
         for name, (res, args) in sig.items():
@@ -370,6 +383,17 @@ class Context:
             arr[i] = self._query_struct(q)
         _check(lib().lp_locpir_batch(self.h, arr, len(queries), _stream(stream)), "lp_locpir_batch")
 
+    def lp_locpir_batch_waves(self, queries: list[dict], mem_budget: int, stream=None) -> int:
+        """As lp_locpir_batch, in waves whose circuits fit mem_budget bytes; returns the number
+        of waves."""
+        arr = (lp_query * len(queries))()
+        for i, q in enumerate(queries):
+            arr[i] = self._query_struct(q)
+        waves = ctypes.c_size_t()
+        _check(lib().lp_locpir_batch_waves(self.h, arr, len(queries), int(mem_budget), ctypes.byref(waves),
+                                           _stream(stream)), "lp_locpir_batch_waves")
+        return waves.value
+
     # ---- alternative product engines
     def lp_set_engines(self, br_engine: int = LP_BR_NTT, ks_engine: int = LP_KS_TABLE) -> None:
         _check(lib().lp_set_engines(self.h, br_engine, ks_engine), "lp_set_engines")
@@ -380,6 +404,28 @@ class Context:
         v = ctypes.c_int()
         _check(lib().lp_autotune(self.h, ctypes.byref(v)), "lp_autotune")
         return v.value
+
+    def lp_autotune_cached(self, cache_path=None, force: bool = False) -> dict:
+        """Measure (or read from the JSON cache file) the launch policy and apply it; returns it."""
+        t = lp_tuning()
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(lib().lp_autotune_cached(self.h, path, int(force), ctypes.byref(t)), "lp_autotune_cached")
+        return {k: getattr(t, k) for k, _ in lp_tuning._fields_}
+
+    def lp_set_tuning(self, split_max: int = 0, tail_split: int = 0, ks_slice_max: int = 0) -> None:
+        t = lp_tuning(split_max, tail_split, ks_slice_max, 0)
+        _check(lib().lp_set_tuning(self.h, ctypes.byref(t)), "lp_set_tuning")
+
+    def lp_selftest_exec_timeout(self, stream=None) -> None:
+        _check(lib().lp_selftest_exec_timeout(self.h, _stream(stream)), "lp_selftest_exec_timeout")
+
+    def lp_set_executor(self, executor: int) -> None:
+        _check(lib().lp_set_executor(self.h, executor), "lp_set_executor")
+
+    def lp_get_tuning(self) -> dict:
+        t = lp_tuning()
+        _check(lib().lp_get_tuning(self.h, ctypes.byref(t)), "lp_get_tuning")
+        return {k: getattr(t, k) for k, _ in lp_tuning._fields_ if k != "from_cache"}
 
     # ---- server-known bounds (beyond the paper)
     def lp_compare_known_batch(self, kind: int, is_signed: int, l: int, x, k, out, count: int, stream=None) -> None:
