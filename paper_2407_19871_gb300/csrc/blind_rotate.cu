@@ -390,22 +390,22 @@ __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
 // ciphertext in sequence), for levels too small to fill the GPU with groups of BR_SLOTS.
 //
 // Per step: every warp rotates/decomposes its own digit row r of ACC, forward-transforms it
-// modulo its prime, multiplies it with its key rows (one Montgomery reduction per product;
-// x < 22p and key < p keep each product below 22 p^2 < 2^32 p, so each reduced product is in
-// [0, 2p)) and adds both output components into the shared partial sums of its prime
-// (shared-memory atomics; 6 terms < 12p < 2^32).  After a barrier, warps (pi, c) for c = 0, 1
-// inverse-transform component c modulo prime pi; after another, all threads recombine both
-// primes (centred CRT) into ACC and clear the partial sums.  Each warp owns an 8 KB key
-// buffer, refilled by its lane 0 with the next step's row right after its MAC (cp.async.bulk,
-// bounded mbarrier wait at the next step).  Steps with abar_i = 0 leave ACC unchanged and
-// are skipped (CTA-uniform), as in br_kernel.
+// modulo its prime and parks the transformed row (lazy, in [0, 22p)) in its transpose buffer.
+// After a barrier, warps (pi, c, h) for the 8 combinations of prime, output component and half
+// of the transform's registers sum the six rows' products with their key rows in 64 bits
+// (x < 22p and key < p: six products stay below 132 p^2 < 2^64), reduce each sum once
+// (Montgomery, then two conditional subtractions: [0, 2p)) and store it.  After a second
+// barrier, each warp refills its key buffer with the next step's row (cp.async.bulk, bounded
+// mbarrier wait at the next step), and warps (pi, c) inverse-transform component c modulo prime
+// pi; after a third, all threads recombine both primes (centred CRT) into ACC.  Steps with
+// abar_i = 0 leave ACC unchanged and are skipped (CTA-uniform), as in br_kernel.
 // ---------------------------------------------------------------------------------
 constexpr int SPLIT_WARPS = 2 * ROWS;
 constexpr int SPLIT_THREADS = SPLIT_WARPS * 32;
 
 struct __align__(16) SplitSmem {
     uint32_t key[SPLIT_WARPS][CHUNK_WORDS];             // 96 KB: this step's row per warp
-    uint32_t tbuf[SPLIT_WARPS][32 * 33];                 // 50 KB
+    uint32_t tbuf[SPLIT_WARPS][32 * 33];                 // 50 KB: transposes, then the parked row
     uint2 tw[2][2][LANE_TW * 32];                        // 31 KB [prime][dir]
     uint32_t part[2][2][RING_N];                         // 16 KB [prime][component]
     uint32_t acc[2][RING_N];                             // 8 KB
@@ -422,7 +422,7 @@ __device__ __forceinline__ void split_issue(SplitSmem &sm, const uint32_t *bsk_h
     bulk_copy_g2s(sm.key[w], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + r) * CHUNK_WORDS, CHUNK_BYTES, &sm.bar[w]);
 }
 
-// Partial sums are stored in transform (layout B) order, index 32 lane + k swizzled to
+// Sums are stored in transform (layout B) order, index 32 lane + k swizzled to
 // 32 lane + (k ^ lane) so that a warp's 32 lanes hit 32 different banks.
 __device__ __forceinline__ int split_pos(int lane, int k) { return lane * 32 + (k ^ lane); }
 
@@ -435,9 +435,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
     const int c_in = r / LG, p_dig = r % LG;
     const int n = a.n;
     const PrimeK K = prime_k(pi);
+    // Roles after the forward transforms: warps 0..7 sum products for (prime, component, half);
+    // warps 0..3 then inverse-transform (prime, component).
+    const int mpi = (warp >> 2) & 1, mc = (warp >> 1) & 1, mh = warp & 1;
+    const PrimeK MK = prime_k(mpi);
+    const int ipi = (warp >> 1) & 1, ic = warp & 1;
+    const PrimeK IK = prime_k(ipi);
 
     for (int i = threadIdx.x; i < 2 * 2 * LANE_TW * 32; i += blockDim.x) (&sm.tw[0][0][0])[i] = a.tw_lane[i];
-    for (int i = threadIdx.x; i < 2 * 2 * RING_N; i += blockDim.x) (&sm.part[0][0][0])[i] = 0u;
     if (threadIdx.x == 0) {
         for (int w = 0; w < SPLIT_WARPS; w++) mbar_init(&sm.bar[w], 1);
         sm.abort = 0;
@@ -466,12 +471,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
         __syncthreads();
         for (int i = 0; i < n; i++) {
             const int ab = sm.abar[i];
-            // This step's key row has landed (bounded wait); refill happens after the MAC.
+            // This step's key row has landed (bounded wait); the refill comes after the sums.
             bool ok = true;
             if (pending) {
                 ok = mbar_wait_bounded(&sm.bar[warp], phase & 1u, &sm.abort);
-                phase++;
-                pending = false;
+                if (ok) {
+                    phase++;
+                    pending = false;   // else the copy stays pending for the drain at exit
+                }
             }
             if (!ok && lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
             if (ab != 0 && ok) {
@@ -488,60 +495,61 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
                     x[k] = ((u >> sh) & 1023u) + (K.p - 512u);
                 }
                 ntt_fwd<false>(x, tbuf, sm.tw[pi][0], lane, pi, K);
-                const uint4 *ch0 = reinterpret_cast<const uint4 *>(sm.key[warp]);
-                const uint4 *ch1 = reinterpret_cast<const uint4 *>(sm.key[warp] + RING_N);
+                // Park the row: register k of lane t at [k][t] (the transform's last transpose
+                // read is behind the warp's synchronisation at its end).
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const uint4 b0 = ch0[q * 32 + lane];
-                    const uint4 b1 = ch1[q * 32 + lane];
-                    const uint32_t bb0[4] = {b0.x, b0.y, b0.z, b0.w};
-                    const uint32_t bb1[4] = {b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int k = 4 * q + e;
-                        atomicAdd(&sm.part[pi][0][split_pos(lane, k)], redc64((unsigned long long)x[k] * bb0[e], K));
-                        atomicAdd(&sm.part[pi][1][split_pos(lane, k)], redc64((unsigned long long)x[k] * bb1[e], K));
-                    }
-                }
+                for (int k = 0; k < 32; k++) tbuf[k * 33 + lane] = x[k];
             }
-            // Refill this warp's key buffer with the next step's row (its reads are done).
-            __syncwarp();
-            if (lane == 0 && ok && i + 1 < n) {
-                fence_proxy_async_smem();
-                split_issue(sm, a.bsk_hat, warp, pi, r, i + 1);
-                pending = true;
-            }
-            pending = __shfl_sync(0xffffffffu, pending ? 1 : 0, 0) != 0;
             if (__syncthreads_or(!ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0)) {
                 aborted = true;
                 break;
             }
-            if (ab == 0) continue;   // CTA-uniform: ACC unchanged, partial sums still zero
-            if (r < 2) {
-                // Warp (pi, c = r): component c modulo prime pi.  Six terms in [0, 2p) sum below
-                // 12p; three conditional subtractions bring them into [0, 2p).
-                const int c = r;
-                uint32_t y[1][32];
+            if (ab != 0 && warp < 8) {
+                // Sums for (prime mpi, component mc), registers k of half mh (blocks of 4).
+                const uint32_t *rows = sm.tbuf[mpi * ROWS];
+#pragma unroll 1
+                for (int q = 4 * mh; q < 4 * mh + 4; q++) {
+                    unsigned long long s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-                for (int k = 0; k < 32; k++) {
-                    uint32_t v = sm.part[pi][c][split_pos(lane, k)];
-                    v = umin_u32(v, v - 4u * K.p2);
-                    v = umin_u32(v, v - 2u * K.p2);
-                    y[0][k] = umin_u32(v, v - K.p2);
+                    for (int rr = 0; rr < ROWS; rr++) {
+                        const uint4 kv = reinterpret_cast<const uint4 *>(sm.key[mpi * ROWS + rr] + mc * RING_N)[q * 32 + lane];
+                        const uint32_t kk[4] = {kv.x, kv.y, kv.z, kv.w};
+                        const uint32_t *xr = rows + rr * 32 * 33;
+#pragma unroll
+                        for (int e = 0; e < 4; e++) s4[e] += (unsigned long long)xr[(4 * q + e) * 33 + lane] * kk[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        uint32_t v = redc64(s4[e], MK);
+                        v = umin_u32(v, v - 2u * MK.p2);
+                        sm.part[mpi][mc][split_pos(lane, 4 * q + e)] = umin_u32(v, v - MK.p2);
+                    }
                 }
-                __syncwarp();
-                ntt_inv_multi<1>(y, tbuf, sm.tw[pi][1], lane, pi, K);
-#pragma unroll
-                for (int k = 0; k < 32; k++) sm.part[pi][c][lane + 32 * k] = umin_u32(y[0][k], y[0][k] - K.p);
             }
             __syncthreads();
-            // ACC += CRT(residues) for both components; clear the partial sums for the next step.
+            // Refill this warp's key buffer with the next step's row (every read of it is done).
+            if (lane == 0 && i + 1 < n) {
+                fence_proxy_async_smem();
+                split_issue(sm, a.bsk_hat, warp, pi, r, i + 1);
+            }
+            pending = i + 1 < n;
+            if (ab == 0) continue;   // CTA-uniform: ACC unchanged
+            if (warp < 4) {
+                // Warp (ipi, ic): component ic modulo prime ipi, sums in [0, 2p).
+                uint32_t y[1][32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) y[0][k] = sm.part[ipi][ic][split_pos(lane, k)];
+                __syncwarp();
+                ntt_inv_multi<1>(y, tbuf, sm.tw[ipi][1], lane, ipi, IK);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 32; k++) sm.part[ipi][ic][lane + 32 * k] = umin_u32(y[0][k], y[0][k] - IK.p);
+            }
+            __syncthreads();
+            // ACC += CRT(residues) for both components.
             for (int t = threadIdx.x; t < 2 * RING_N; t += blockDim.x) {
                 const int c = t / RING_N, j = t % RING_N;
-                const uint32_t x0 = sm.part[0][c][j], x1 = sm.part[1][c][j];
-                sm.part[0][c][j] = 0u;
-                sm.part[1][c][j] = 0u;
-                sm.acc[c][j] += crt_lift(x0, x1);
+                sm.acc[c][j] += crt_lift(sm.part[0][c][j], sm.part[1][c][j]);
             }
             __syncthreads();
         }
