@@ -60,8 +60,10 @@ KS_SMEM_BYTES_PER_CT = 1024 * 4 * 632 * 4
 SMEM_BYTES_PER_CLK_SM = 128
 
 
-# Per-device cache of the autotuner's choices (lp_autotune_cached), beside the build outputs.
+# Per-device cache of the autotuner's choices (lp_autotune_cached), beside the build outputs;
+# --retune measures again whatever the cache holds (so every run launches the same kernels).
 TUNING_CACHE = os.environ.get("LOCPIR_TUNING_CACHE", os.path.join(ROOT, "_build", "tuning.json"))
+RETUNE = False
 
 
 def _dist():
@@ -169,7 +171,7 @@ def setup_gpu(local: int, seed_keys: int = 0, seed_inputs: int = 1, count: int =
     del bsk, ksk
     # launch policy measured on this GPU (or read from the per-device cache written by an earlier run)
     os.makedirs(os.path.dirname(TUNING_CACHE), exist_ok=True)
-    ctx.tuning = ctx.lp_autotune_cached(TUNING_CACHE)
+    ctx.tuning = ctx.lp_autotune_cached(TUNING_CACHE, force=RETUNE)
     ctx.split_max = ctx.tuning["split_max"]
     A, B = synth.nand_pairs(seed_inputs, count)
     cts = []
@@ -1056,8 +1058,11 @@ def main():
     ap.add_argument("--serve-policy", default="queue", choices=["queue", "reject"])
     ap.add_argument("--count", type=int, default=COUNT,
                     help="gates per step (default 65,536; smaller values are for profiling only)")
+    ap.add_argument("--retune", action="store_true", help="measure the launch policy again instead of reading its cache")
     args = ap.parse_args()
     COUNT = args.count
+    global RETUNE
+    RETUNE = args.retune
     if args.int_peaks:
         sys.exit(int_peaks())
     if args.multibox:

@@ -393,12 +393,13 @@ __global__ void __launch_bounds__(BR_THREADS, 1) br_kernel(BrArgs a)
 // modulo its prime and parks the transformed row (lazy, in [0, 22p)) in its transpose buffer.
 // After a barrier, warps (pi, c, h) for the 8 combinations of prime, output component and half
 // of the transform's registers sum the six rows' products with their key rows in 64 bits
-// (x < 22p and key < p: six products stay below 132 p^2 < 2^64), reduce each sum once
-// (Montgomery, then two conditional subtractions: [0, 2p)) and store it.  After a second
-// barrier, each warp refills its key buffer with the next step's row (cp.async.bulk, bounded
-// mbarrier wait at the next step), and warps (pi, c) inverse-transform component c modulo prime
-// pi; after a third, all threads recombine both primes (centred CRT) into ACC.  Steps with
-// abar_i = 0 leave ACC unchanged and are skipped (CTA-uniform), as in br_kernel.
+// (x < 22p and key < p: six products stay below 132 p^2 < 2^64) and reduce each sum once
+// (Montgomery, then two conditional subtractions: [0, 2p)), keeping it in registers.  After a
+// second barrier, each warp refills its key buffer with the next step's row (cp.async.bulk,
+// bounded mbarrier wait at the next step), and the two warps of each (pi, c) inverse-transform
+// component c modulo prime pi together (ntt_inv_2warp); after a third, all threads recombine
+// both primes (centred CRT) into ACC.  Steps with abar_i = 0 leave ACC unchanged and are
+// skipped (CTA-uniform), as in br_kernel.
 // ---------------------------------------------------------------------------------
 constexpr int SPLIT_WARPS = 2 * ROWS;
 constexpr int SPLIT_THREADS = SPLIT_WARPS * 32;
@@ -422,6 +423,83 @@ __device__ __forceinline__ void split_issue(SplitSmem &sm, const uint32_t *bsk_h
     bulk_copy_g2s(sm.key[w], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + r) * CHUNK_WORDS, CHUNK_BYTES, &sm.bar[w]);
 }
 
+// Inverse transform of one polynomial by two warps: warp h holds registers 16 h .. 16 h + 15
+// of layout B (lane t, register k = index 32 t + k), 16 values y[i] per lane, in [0, 2p).
+// Stages 9..6 pair registers within a half; stage 5 (pairs k, k + 16) and stage 0 (layout A,
+// pairs k', k' + 16) cross the halves, so the warps swap 8 values per lane through X (512
+// words) and each computes half of those butterflies; the layout B -> A transpose goes through
+// TB (32 x 33 words).  The warps meet at named barrier bar_id (64 threads).  On return y[i],
+// in [0, 2p), is the natural-order coefficient lane + 32 k' with k' = 8 h + i (i < 8) or
+// 16 + 8 h + (i - 8).
+__device__ __forceinline__ void ntt_inv_2warp(uint32_t (&y)[16], int h, int lane, int pi, const PrimeK &K,
+                                              const uint2 *twi, uint32_t *TB, uint32_t *X, int bar_id)
+{
+#pragma unroll
+    for (int s = 9; s >= 6; s--) {
+        const int L = 16 >> (s - 5);
+        const int base = (1 << (s - 5)) - 1;
+#pragma unroll
+        for (int bl = 0; bl < 16 / (2 * L); bl++) {
+            const uint2 z = twi[(base + (16 * h) / (2 * L) + bl) * 32 + lane];
+#pragma unroll
+            for (int o = 0; o < L; o++) bfly_inv(y[bl * 2 * L + o], y[bl * 2 * L + o + L], z.x, z.y, K);
+        }
+    }
+    // Stage 5: warp 0 computes the pairs (k, k + 16) for k < 8, warp 1 those for 8 <= k < 16.
+    uint32_t *out = X + h * 256;
+    const uint32_t *in = X + (1 - h) * 256;
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i * 32 + lane] = h == 0 ? y[8 + i] : y[i];
+    bar_red_or(bar_id, 64, false);
+    {
+        const uint2 z = twi[lane];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            uint32_t a = h == 0 ? y[i] : in[i * 32 + lane];
+            uint32_t b = h == 0 ? in[i * 32 + lane] : y[8 + i];
+            bfly_inv(a, b, z.x, z.y, K);
+            y[i] = a;
+            y[8 + i] = b;
+        }
+    }
+    // Layout B -> A: values at registers 8 h + i and 16 + 8 h + i of lane t.
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        TB[lane * 33 + 8 * h + i] = y[i];
+        TB[lane * 33 + 16 + 8 * h + i] = y[8 + i];
+    }
+    bar_red_or(bar_id, 64, false);
+#pragma unroll
+    for (int i = 0; i < 16; i++) y[i] = TB[(16 * h + i) * 33 + lane];
+    // Stages 4..1 within the half (registers k' = 16 h + i of layout A).
+#pragma unroll
+    for (int s = 4; s >= 1; s--) {
+        const int D = 16 >> s;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            if (i & D) continue;
+            const uint2 z = c_tw[pi][1][(1 << s) + ((16 * h + i) >> (5 - s))];
+            bfly_inv(y[i], y[i + D], z.x, z.y, K);
+        }
+    }
+    // Stage 0 (pairs k', k' + 16), split as stage 5.  X was last read before the transpose's
+    // barrier, so it may be written again.
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i * 32 + lane] = h == 0 ? y[8 + i] : y[i];
+    bar_red_or(bar_id, 64, false);
+    {
+        const uint2 z = c_tw[pi][1][1];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            uint32_t a = h == 0 ? y[i] : in[i * 32 + lane];
+            uint32_t b = h == 0 ? in[i * 32 + lane] : y[8 + i];
+            bfly_inv(a, b, z.x, z.y, K);
+            y[i] = a;
+            y[8 + i] = b;
+        }
+    }
+}
+
 // Sums are stored in transform (layout B) order, index 32 lane + k swizzled to
 // 32 lane + (k ^ lane) so that a warp's 32 lanes hit 32 different banks.
 __device__ __forceinline__ int split_pos(int lane, int k) { return lane * 32 + (k ^ lane); }
@@ -435,12 +513,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
     const int c_in = r / LG, p_dig = r % LG;
     const int n = a.n;
     const PrimeK K = prime_k(pi);
-    // Roles after the forward transforms: warps 0..7 sum products for (prime, component, half);
-    // warps 0..3 then inverse-transform (prime, component).
+    // Roles after the forward transforms: warp 4 mpi + 2 mc + mh (< 8) sums the products of
+    // (prime mpi, output component mc) for half mh of the registers, then inverse-transforms
+    // that half together with its partner warp.
     const int mpi = (warp >> 2) & 1, mc = (warp >> 1) & 1, mh = warp & 1;
     const PrimeK MK = prime_k(mpi);
-    const int ipi = (warp >> 1) & 1, ic = warp & 1;
-    const PrimeK IK = prime_k(ipi);
 
     for (int i = threadIdx.x; i < 2 * 2 * LANE_TW * 32; i += blockDim.x) (&sm.tw[0][0][0])[i] = a.tw_lane[i];
     if (threadIdx.x == 0) {
@@ -504,11 +581,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
                 aborted = true;
                 break;
             }
+            // Sums for (prime mpi, component mc), registers k = 16 mh + i of layout B (blocks of 4),
+            // kept in registers for this pair of warps' inverse transform.
+            uint32_t ys[16];
             if (ab != 0 && warp < 8) {
-                // Sums for (prime mpi, component mc), registers k of half mh (blocks of 4).
                 const uint32_t *rows = sm.tbuf[mpi * ROWS];
-#pragma unroll 1
-                for (int q = 4 * mh; q < 4 * mh + 4; q++) {
+#pragma unroll
+                for (int qq = 0; qq < 4; qq++) {
+                    const int q = 4 * mh + qq;
                     unsigned long long s4[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
                     for (int rr = 0; rr < ROWS; rr++) {
@@ -522,7 +602,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
                     for (int e = 0; e < 4; e++) {
                         uint32_t v = redc64(s4[e], MK);
                         v = umin_u32(v, v - 2u * MK.p2);
-                        sm.part[mpi][mc][split_pos(lane, 4 * q + e)] = umin_u32(v, v - MK.p2);
+                        ys[4 * qq + e] = umin_u32(v, v - MK.p2);
                     }
                 }
             }
@@ -534,16 +614,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
             }
             pending = i + 1 < n;
             if (ab == 0) continue;   // CTA-uniform: ACC unchanged
-            if (warp < 4) {
-                // Warp (ipi, ic): component ic modulo prime ipi, sums in [0, 2p).
-                uint32_t y[1][32];
+            if (warp < 8) {
+                // Component mc modulo prime mpi by warps (mpi, mc, 0) and (mpi, mc, 1), through the
+                // transpose buffers of that warp pair (the parked rows are all read).
+                const int w0 = 4 * mpi + 2 * mc;
+                ntt_inv_2warp(ys, mh, lane, mpi, MK, sm.tw[mpi][1], sm.tbuf[w0], sm.tbuf[w0 + 1], 1 + 2 * mpi + mc);
 #pragma unroll
-                for (int k = 0; k < 32; k++) y[0][k] = sm.part[ipi][ic][split_pos(lane, k)];
-                __syncwarp();
-                ntt_inv_multi<1>(y, tbuf, sm.tw[ipi][1], lane, ipi, IK);
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k < 32; k++) sm.part[ipi][ic][lane + 32 * k] = umin_u32(y[0][k], y[0][k] - IK.p);
+                for (int i = 0; i < 16; i++) {
+                    const int kk = i < 8 ? 8 * mh + i : 16 + 8 * mh + (i - 8);
+                    sm.part[mpi][mc][lane + 32 * kk] = umin_u32(ys[i], ys[i] - MK.p);
+                }
             }
             __syncthreads();
             // ACC += CRT(residues) for both components.
