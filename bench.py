@@ -593,7 +593,7 @@ def _random_query_time(ctx, p, s_dev, l: int, nb: int, m: int, seed: int) -> tup
     return sec, wrong
 
 
-def paper_shapes() -> None:
+def paper_shapes(table2_only: bool = False) -> None:
     import torch
     from paper_2407_19871_gb300 import locpir
     table = json.load(open(os.path.join(ROOT, "tests", "golden", "table1.json")))["rows"]
@@ -648,7 +648,7 @@ def paper_shapes() -> None:
                               "paper_seconds_total": {(540, 13): 4.36, (630, 13): 4.88, (540, 16): 5.12,
                                                       (630, 16): 5.67}[(n, l)],
                               "paper_hardware": "Ryzen 5 3500X, TFHE library v1.1 (Table 2)"}), flush=True)
-        if n == 630:
+        if n == 630 and not table2_only:
             # Fig. 4(a): time against (B_x, l) at m = 9; the paper prints its B_x = 10 row.
             paper4a = {8: 3.256, 16: 6.139, 24: 8.764, 32: 11.670}
             for nb in (2, 4, 6, 8, 10, 16, 28):
@@ -1034,6 +1034,7 @@ def main():
                     help="LocPIR queries of the city-batch shape timed for queries/s (0: skip)")
     ap.add_argument("--paper-shapes", action="store_true",
                     help="run the paper's experiment shapes (Table 2, Fig. 4(a), batch width); one JSON line each")
+    ap.add_argument("--table2-only", action="store_true", help="with --paper-shapes: Table 2's four rows only")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson arrivals into the query server")
     ap.add_argument("--engines", action="store_true",
                     help="head-to-head of the NTT and tensor-core (GEMM) engines instead of the bench line")
@@ -1068,7 +1069,7 @@ def main():
     if args.multibox:
         multibox_uneven(args)
     elif args.paper_shapes:
-        paper_shapes()
+        paper_shapes(args.table2_only)
     elif args.serve:
         serve(args)
     elif args.engines:
