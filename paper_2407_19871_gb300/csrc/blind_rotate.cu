@@ -650,6 +650,272 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
 }
 
 // ---------------------------------------------------------------------------------
+// Paired split blind rotation: one ciphertext per cluster of two CTAs on two SMs, for levels
+// of at most one ciphertext per two SMs.  CTA rank q of the cluster computes modulo NTT prime
+// q only, on 6 warps: warp r rotates, decomposes and forward-transforms digit row r and parks
+// it (as in br_split_kernel); warps (mc, mh) < 4 sum the six rows' products with the key rows
+// of output component mc for half mh of the registers (64-bit sums, one reduction each) and
+// inverse-transform component mc together (ntt_inv_2warp).  Each CTA writes its residues of
+// both components into its own shared memory and, with st.async, into its partner's, so that
+// after one exchange per step both CTAs hold all four residue polynomials and each recombines
+// both components (centred CRT) into its own copy of ACC; the two copies stay equal.
+//
+// Exchange s lands in buffer set s & 1 and completes on the receiver's mbarrier xbar[s & 1]:
+// the receiver arms it once per exchange (one arrival, PAIR_XCHG_BYTES expected), and every
+// st.async of the sender counts its bytes on it (release at cluster scope); the receiver's
+// bounded wait acquires at cluster scope.  A sender reaches exchange s + 1 only after it has
+// received exchange s, so it is at most one exchange ahead: the other set and the other
+// barrier.  The sender's status word (1: a key copy timed out) is part of each exchange, so a
+// CTA that stops makes its partner stop after the same exchange; a stopping CTA still sends
+// every byte, which keeps the count exact.  The exchange waits allow four times the key
+// waits' limit.  The hardware cluster barrier is used only at entry (the partner's barriers
+// are initialised before the first st.async) and at exit (no CTA leaves while its partner may
+// still write to it), both reached unconditionally.
+// ---------------------------------------------------------------------------------
+constexpr int PAIR_WARPS = ROWS;
+constexpr int PAIR_THREADS = PAIR_WARPS * 32;
+constexpr uint64_t PAIR_XCHG_LIMIT_NS = 4 * WAIT_LIMIT_NS;
+constexpr uint32_t PAIR_XCHG_BYTES = 2u * RING_N * 4u + 4u;   // both components + status word
+
+struct __align__(16) PairSmem {
+    uint32_t key[ROWS][CHUNK_WORDS];                     // 48 KB: this step's rows for this CTA's prime
+    uint32_t tbuf[ROWS][32 * 33];                         // 24.8 KB: transposes, then the parked rows
+    uint2 tw[2][LANE_TW * 32];                            // 15.5 KB [dir] for this CTA's prime
+    uint32_t res[2][2][2][RING_N];                        // 32 KB [exchange set][prime][component]
+    uint32_t acc[2][RING_N];                              // 8 KB
+    uint16_t abar[ABAR_STRIDE_MAX];                       // 2 KB
+    uint64_t bar[ROWS];                                   // key copies, one per row
+    uint64_t xbar[2];                                     // exchanges, by set
+    uint32_t status[2];                                   // the partner's status, by set
+    int abort;                                            // a key wait of this CTA gave up
+};
+
+size_t br_pair_smem_bytes() { return sizeof(PairSmem); }
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// The address of the same shared-memory location in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t mapa_shared(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// Store to another CTA's shared memory that counts its 4 bytes on that CTA's mbarrier.
+__device__ __forceinline__ void st_async_u32(uint32_t addr, uint32_t v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.u32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+                 "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void hw_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 "
+        "%0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+__device__ __forceinline__ bool pair_wait_xchg(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((it & 255u) == 0u && global_timer_ns() - t0 > PAIR_XCHG_LIMIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void pair_issue(PairSmem &sm, const uint32_t *bsk_hat, int pi, int r, int i)
+{
+    mbar_arrive_expect_tx(&sm.bar[r], CHUNK_BYTES);
+    bulk_copy_g2s(sm.key[r], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + r) * CHUNK_WORDS, CHUNK_BYTES, &sm.bar[r]);
+}
+
+__global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    PairSmem &sm = *reinterpret_cast<PairSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pi = (int)cluster_ctarank();   // this CTA's prime
+    const uint32_t peer = 1u - (uint32_t)pi;
+    const int r = warp, c_in = r / LG, p_dig = r % LG;
+    const int n = a.n;
+    const PrimeK K = prime_k(pi);
+    const int mc = warp >> 1, mh = warp & 1;   // warps 0..3 after the forward transforms
+    const uint32_t peer_res = mapa_shared(&sm.res[0][0][0][0], peer);
+    const uint32_t peer_xbar = mapa_shared(&sm.xbar[0], peer);
+    const uint32_t peer_status = mapa_shared(&sm.status[0], peer);
+
+    for (int i = threadIdx.x; i < 2 * LANE_TW * 32; i += blockDim.x)
+        (&sm.tw[0][0])[i] = a.tw_lane[(size_t)pi * 2 * LANE_TW * 32 + i];
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < ROWS; w++) mbar_init(&sm.bar[w], 1);
+        mbar_init(&sm.xbar[0], 1);
+        mbar_init(&sm.xbar[1], 1);
+        sm.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    hw_cluster_sync();   // both CTAs' barriers are initialised
+
+    uint32_t *tbuf = sm.tbuf[warp];
+    uint32_t phase = 0;        // completed uses of this warp's key barrier
+    uint32_t xs = 0;           // exchanges done
+    bool pending = false;      // a copy into this warp's key buffer is in flight
+    bool aborted = false;
+    const int clusters = (int)(gridDim.x >> 1);
+    for (int job = (int)(blockIdx.x >> 1); job < a.jobs && !aborted; job += clusters) {
+        const uint16_t *src = a.abar + (size_t)job * a.abar_stride;
+        for (int i = threadIdx.x; i <= n; i += blockDim.x) sm.abar[i] = src[i];
+        __syncthreads();
+        const int bb = sm.abar[n];
+        for (int j = threadIdx.x; j < RING_N; j += blockDim.x) {
+            sm.acc[0][j] = 0u;
+            const int e = (j + bb) & (2 * RING_N - 1);
+            sm.acc[1][j] = (e & RING_N) ? (0u - a.mu) : a.mu;
+        }
+        if (n > 0) {
+            if (lane == 0) pair_issue(sm, a.bsk_hat, pi, r, 0);
+            pending = true;
+        }
+        __syncthreads();
+        for (int i = 0; i < n; i++) {
+            const int ab = sm.abar[i];   // both CTAs run the same job: the same decisions
+            const int set = (int)(xs & 1u);
+            // Arm this exchange's barrier (its previous phase completed two exchanges ago).
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(&sm.xbar[set], PAIR_XCHG_BYTES);
+            bool ok = true;
+            if (pending) {
+                ok = mbar_wait_bounded(&sm.bar[r], phase & 1u, &sm.abort);
+                if (ok) {
+                    phase++;
+                    pending = false;   // else the copy stays pending for the drain at exit
+                }
+            }
+            if (!ok && lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+            if (ab != 0 && ok) {
+                const uint32_t *A = sm.acc[c_in];
+                const int sh = 32 - BGBIT * (p_dig + 1);
+                uint32_t x[32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    const int j = lane + 32 * k;
+                    const int idx = (j - ab) & (2 * RING_N - 1);
+                    uint32_t v = A[idx & (RING_N - 1)];
+                    v = (idx & RING_N) ? (0u - v) : v;
+                    const uint32_t u = v - A[j] + GADGET_OFF;
+                    x[k] = ((u >> sh) & 1023u) + (K.p - 512u);
+                }
+                ntt_fwd<false>(x, tbuf, sm.tw[0], lane, pi, K);
+#pragma unroll
+                for (int k = 0; k < 32; k++) tbuf[k * 33 + lane] = x[k];
+            }
+            const bool bad = __syncthreads_or(!ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
+            const bool work = !bad && ab != 0;
+            uint32_t ys[16];
+#pragma unroll
+            for (int t = 0; t < 16; t++) ys[t] = 0u;
+            if (work && warp < 4) {
+#pragma unroll
+                for (int qq = 0; qq < 4; qq++) {
+                    const int q = 4 * mh + qq;
+                    unsigned long long s4[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+                    for (int rr = 0; rr < ROWS; rr++) {
+                        const uint4 kv = reinterpret_cast<const uint4 *>(sm.key[rr] + mc * RING_N)[q * 32 + lane];
+                        const uint32_t kk[4] = {kv.x, kv.y, kv.z, kv.w};
+                        const uint32_t *xr = sm.tbuf[rr];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) s4[e] += (unsigned long long)xr[(4 * q + e) * 33 + lane] * kk[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        uint32_t v = redc64(s4[e], K);
+                        v = umin_u32(v, v - 2u * K.p2);
+                        ys[4 * qq + e] = umin_u32(v, v - K.p2);
+                    }
+                }
+            }
+            __syncthreads();
+            // Refill this warp's key buffer with the next step's row (every read of it is done).
+            if (!bad && lane == 0 && i + 1 < n) {
+                fence_proxy_async_smem();
+                pair_issue(sm, a.bsk_hat, pi, r, i + 1);
+            }
+            if (!bad && i + 1 < n) pending = true;
+            if (warp < 4) {
+                // Component mc modulo this CTA's prime by warps (mc, 0) and (mc, 1), through the
+                // transpose buffers of rows 2 mc and 2 mc + 1 (all parked rows are read).
+                if (work) ntt_inv_2warp(ys, mh, lane, pi, K, sm.tw[1], sm.tbuf[2 * mc], sm.tbuf[2 * mc + 1], 1 + mc);
+                const int off = ((set * 2 + pi) * 2 + mc) * RING_N;
+                uint32_t *dst = &sm.res[0][0][0][0] + off;
+                const uint32_t rdst = peer_res + 4u * (uint32_t)off;
+                const uint32_t rbar = peer_xbar + 8u * (uint32_t)set;
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int kk = t < 8 ? 8 * mh + t : 16 + 8 * mh + (t - 8);
+                    const int j = lane + 32 * kk;
+                    const uint32_t v = umin_u32(ys[t], ys[t] - K.p);
+                    dst[j] = v;
+                    st_async_u32(rdst + 4u * (uint32_t)j, v, rbar);
+                }
+                if (threadIdx.x == 0)
+                    st_async_u32(peer_status + 4u * (uint32_t)set, bad ? 1u : 0u, rbar);
+            }
+            const bool arrived = pair_wait_xchg(&sm.xbar[set], (xs >> 1) & 1u);
+            xs++;
+            const bool stop =
+                __syncthreads_or(bad || !arrived || *reinterpret_cast<volatile uint32_t *>(&sm.status[set]) != 0u);
+            if (stop) {
+                aborted = true;
+                break;
+            }
+            if (ab != 0) {
+                // ACC += CRT(residues) for both components, from this exchange's set.
+                for (int t = threadIdx.x; t < 2 * RING_N; t += blockDim.x) {
+                    const int c = t / RING_N, j = t % RING_N;
+                    sm.acc[c][j] += crt_lift(sm.res[set][0][c][j], sm.res[set][1][c][j]);
+                }
+            }
+            __syncthreads();
+        }
+        if (aborted) break;
+        // Sample extraction (both copies of ACC are equal; CTA 0 writes the sample).
+        if (pi == 0) {
+            uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
+            for (int j = threadIdx.x; j < RING_N; j += blockDim.x)
+                dst[j] = j == 0 ? sm.acc[0][0] : 0u - sm.acc[0][RING_N - j];
+            if (threadIdx.x == 0) dst[RING_N] = sm.acc[1][0];
+        }
+        __syncthreads();
+    }
+    if (aborted && threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    // No bulk copy may still be in flight when the CTA exits (only possible after an abort).
+    if (lane == 0 && pending) {
+        volatile int never = 0;
+        if (!mbar_wait_bounded(&sm.bar[r], phase & 1u, &never)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    }
+    hw_cluster_sync();   // the partner no longer writes to this CTA's shared memory
+}
+
+// ---------------------------------------------------------------------------------
 // Bootstrapping key -> transform domain.  One warp per (i, prime, row, component)
 // polynomial: centred lift mod p, forward NTT, scale by N^-1 2^32 mod p, store in the
 // chunk layout the blind rotation reads (component c, then [q][lane][4] so that lane t
@@ -923,6 +1189,55 @@ static cudaError_t launch_split(const BrArgs &a, int num_sms, cudaStream_t st)
     return cudaGetLastError();
 }
 
+static cudaError_t pair_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int clusters, cudaStream_t st)
+{
+    const size_t smem = sizeof(PairSmem);
+    cudaError_t e = cudaFuncSetAttribute(br_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3((unsigned)(2 * clusters));
+    cfg.blockDim = dim3(PAIR_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaSuccess;
+}
+
+int br_pair_clusters(int num_sms)
+{
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (pair_config(cfg, attr, num_sms / 2, nullptr) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, br_pair_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+static cudaError_t launch_pair(const BrArgs &a, int num_sms, cudaStream_t st)
+{
+    const int clusters = a.jobs < num_sms / 2 ? a.jobs : num_sms / 2;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = pair_config(cfg, attr, clusters, st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, br_pair_kernel, a);
+}
+
+// Levels (or remainders) small enough for one CTA or CTA pair per ciphertext: paired when
+// they fit pair_max clusters, else split.
+static cudaError_t launch_small(const BrArgs &a, int num_sms, cudaStream_t st, int pair_max)
+{
+    return a.jobs <= pair_max ? launch_pair(a, num_sms, st) : launch_split(a, num_sms, st);
+}
+
 static cudaError_t launch_batched(const BrArgs &a, int num_sms, cudaStream_t st)
 {
     const size_t smem = sizeof(BrSmem);
@@ -936,24 +1251,30 @@ static cudaError_t launch_batched(const BrArgs &a, int num_sms, cudaStream_t st)
 
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
-                      cudaStream_t st, int variant, int split_max, int tail_split, int *launched)
+                      cudaStream_t st, int variant, int split_max, int tail_split, int pair_max, int *launched)
 {
     if (launched) *launched = 0;
     if (jobs <= 0) return cudaSuccess;
     BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
-    // Policy (measured on GB300): a split CTA finishes one ciphertext in 4.4-4.8 ms, a batched
+    if (variant == BR_VARIANT_PAIR) {
+        if (launched) *launched = 1;
+        return launch_pair(a, num_sms, st);
+    }
+    // Policy (measured on GB300): a split CTA finishes one ciphertext in about 4 ms, a batched
     // wave of up to 4 per SM takes 13.3-14.3 ms, so levels of up to two ciphertexts per SM run
     // split (one or two split waves) and larger ones batched, unless lp_autotune measured
-    // another crossing on this device.
+    // another crossing on this device.  Levels that fit pair_max clusters of two SMs run on the
+    // paired kernel instead.
     const int smax = split_max > 0 ? split_max : 2 * num_sms;
+    const int pmax = variant == BR_VARIANT_AUTO ? pair_max : 0;
     const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= smax);
     if (split) {
         if (launched) *launched = 1;
-        return launch_split(a, num_sms, st);
+        return launch_small(a, num_sms, st, pmax);
     }
     // A wider level whose last batched wave would be partial: with tail_split (chosen by the
     // autotuner), the full waves run batched and the remainder, when it is within the split
-    // crossing, on the split kernel, which finishes it in a fraction of a batched wave.
+    // crossing, on the split (or paired) kernel, which finishes it in a fraction of a batched wave.
     const int wave = BR_SLOTS * num_sms;
     const int rem = jobs % wave;
     if (variant == BR_VARIANT_AUTO && tail_split && rem > 0 && rem <= smax && jobs > rem) {
@@ -963,7 +1284,7 @@ cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, cons
         tail.abar = abar + (size_t)head.jobs * abar_stride;
         tail.ext = ext + (size_t)head.jobs * EXT_STRIDE;
         cudaError_t e = launch_batched(head, num_sms, st);
-        if (e == cudaSuccess) e = launch_split(tail, num_sms, st);
+        if (e == cudaSuccess) e = launch_small(tail, num_sms, st, pmax);
         if (launched) *launched = 2;
         return e;
     }

@@ -184,6 +184,7 @@ extern "C" int lp_create(const lp_params *p, int device, lp_ctx **out)
     c->params = *p;
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
+    c->br_pair_clusters = br_pair_clusters(c->num_sms);
     build_ntt_tables(c->tables);
     if ((e = upload_constants(c->tables)) != cudaSuccess) {
         delete c;
@@ -412,6 +413,16 @@ int lp::ensure_scratch(lp_ctx *c, size_t br_jobs)
     return rc;
 }
 
+int lp::br_variant(const lp_ctx *c)
+{
+    switch (c->br_engine) {
+    case LP_BR_NTT_BATCHED: return BR_VARIANT_BATCHED;
+    case LP_BR_NTT_SPLIT: return BR_VARIANT_SPLIT;
+    case LP_BR_NTT_PAIR: return BR_VARIANT_PAIR;
+    default: return BR_VARIANT_AUTO;
+    }
+}
+
 int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
 {
     cudaEvent_t ev0;
@@ -421,15 +432,13 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
         timer_end(c, "br", st, ev0);
         return rc;
     }
-    const int variant = c->br_engine == LP_BR_NTT_BATCHED ? BR_VARIANT_BATCHED
-                        : c->br_engine == LP_BR_NTT_SPLIT ? BR_VARIANT_SPLIT
-                                                          : BR_VARIANT_AUTO;
+    const int variant = br_variant(c);
     int launched = 0;
     cudaError_t e = launch_br(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
                               static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max,
-                              c->br_tail_split, &launched);
+                              c->br_tail_split, br_pair_limit(c), &launched);
     timer_end(c, "br", st, ev0);
     c->launches += launched;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
@@ -458,7 +467,7 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
 extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
 {
     if (!c) return fail(LP_EINVAL, "null context");
-    if (br_engine < LP_BR_NTT || br_engine > LP_BR_NTT_SPLIT)
+    if (br_engine < LP_BR_NTT || br_engine > LP_BR_NTT_PAIR)
         return fail(LP_EINVAL, "unknown blind-rotation engine %d", br_engine);
     if (ks_engine < LP_KS_TABLE || ks_engine > LP_KS_TENSOR_INT8)
         return fail(LP_EINVAL, "unknown key-switch engine %d", ks_engine);
@@ -536,6 +545,26 @@ static int measure_tuning(lp_ctx *c, lp_tuning *t)
     for (int k = 2; k <= 4 && tb[k][1] < tb[k][0]; k++) best = k * S;
     t->split_max = best;
     t->tail_split = tb[1][1] < tb[1][0] ? 1 : 0;
+    // Paired against split at one ciphertext per resident cluster (half the SMs at most).
+    t->pair_max = -1;
+    const int pc = c->br_pair_clusters;
+    if (pc > 0) {
+        float tp[2] = {};
+        for (int v = 0; v < 2 && e == cudaSuccess; v++) {
+            const int variant = v ? BR_VARIANT_PAIR : BR_VARIANT_SPLIT;
+            e = time_median(
+                [&] {
+                    c->launches++;
+                    return launch_br(static_cast<const uint16_t *>(c->abar.ptr), stride,
+                                     static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                                     static_cast<const uint2 *>(c->tw_lane.ptr), n, pc, T_EIGHTH,
+                                     static_cast<int *>(c->err.ptr), S, 0, variant);
+                },
+                &tp[v]);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "autotune paired blind rotation");
+        if (tp[1] < tp[0]) t->pair_max = pc;
+    }
     // Key switch: sliced against whole-table CTAs at 1/4 .. 1 batch per SM (64 outputs each),
     // on the extracted samples the blind rotations just wrote.
     DevBuf out;
@@ -573,6 +602,7 @@ static void apply_tuning(lp_ctx *c, const lp_tuning &t)
     c->br_split_max = t.split_max;
     c->br_tail_split = t.tail_split;
     c->ks_slice_max = t.ks_slice_max;
+    c->br_pair_max = t.pair_max;
 }
 
 extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
@@ -626,14 +656,17 @@ static bool read_tuning(const char *path, const std::string &key, lp_tuning *t)
         return end != txt.c_str() + p;
     };
     std::string k;
-    long sm = 0, ts = 0, ks = 0;
+    long sm = 0, ts = 0, ks = 0, pm = 0;
     if (!field("key", &k, nullptr) || k != key) return false;
-    if (!field("split_max", nullptr, &sm) || !field("tail_split", nullptr, &ts) || !field("ks_slice_max", nullptr, &ks))
+    if (!field("split_max", nullptr, &sm) || !field("tail_split", nullptr, &ts) || !field("ks_slice_max", nullptr, &ks) ||
+        !field("pair_max", nullptr, &pm))
         return false;
-    if (sm < 1 || sm > 1 << 20 || (ts != 0 && ts != 1) || ks < -1 || ks > 1 << 20) return false;
+    if (sm < 1 || sm > 1 << 20 || (ts != 0 && ts != 1) || ks < -1 || ks > 1 << 20 || pm < -1 || pm > 1 << 20)
+        return false;
     t->split_max = (int)sm;
     t->tail_split = (int)ts;
     t->ks_slice_max = (int)ks;
+    t->pair_max = (int)pm;
     return true;
 }
 
@@ -644,8 +677,8 @@ static int write_tuning(const char *path, const std::string &key, const lp_tunin
     if (!f) return fail(LP_EINVAL, "cannot write the tuning cache %s", tmp.c_str());
     std::string k;
     for (char ch : key) k += (ch == '"' || ch == '\\') ? '_' : ch;
-    fprintf(f, "{\"key\": \"%s\", \"split_max\": %d, \"tail_split\": %d, \"ks_slice_max\": %d}\n", k.c_str(),
-            t.split_max, t.tail_split, t.ks_slice_max);
+    fprintf(f, "{\"key\": \"%s\", \"split_max\": %d, \"tail_split\": %d, \"ks_slice_max\": %d, \"pair_max\": %d}\n",
+            k.c_str(), t.split_max, t.tail_split, t.ks_slice_max, t.pair_max);
     const bool ok = fclose(f) == 0;
     if (!ok || rename(tmp.c_str(), path) != 0) return fail(LP_EINVAL, "cannot write the tuning cache %s", path);
     return LP_OK;
@@ -691,9 +724,9 @@ extern "C" int lp_set_executor(lp_ctx *c, int executor)
 extern "C" int lp_set_tuning(lp_ctx *c, const lp_tuning *t)
 {
     if (!c || !t) return fail(LP_EINVAL, "null argument");
-    if (t->split_max < 0 || (t->tail_split != 0 && t->tail_split != 1) || t->ks_slice_max < -1)
-        return fail(LP_EINVAL, "invalid tuning (split_max %d, tail_split %d, ks_slice_max %d)", t->split_max,
-                    t->tail_split, t->ks_slice_max);
+    if (t->split_max < 0 || (t->tail_split != 0 && t->tail_split != 1) || t->ks_slice_max < -1 || t->pair_max < -1)
+        return fail(LP_EINVAL, "invalid tuning (split_max %d, tail_split %d, ks_slice_max %d, pair_max %d)",
+                    t->split_max, t->tail_split, t->ks_slice_max, t->pair_max);
     apply_tuning(c, *t);
     return LP_OK;
 }
@@ -705,6 +738,7 @@ extern "C" int lp_get_tuning(const lp_ctx *c, lp_tuning *t)
     t->split_max = c->br_split_max;
     t->tail_split = c->br_tail_split;
     t->ks_slice_max = c->ks_slice_max;
+    t->pair_max = c->br_pair_max;
     return LP_OK;
 }
 

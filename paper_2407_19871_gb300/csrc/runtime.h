@@ -45,6 +45,8 @@ struct lp_ctx {
     int br_engine = LP_BR_NTT, ks_engine = LP_KS_TABLE;
     int br_split_max = 0;           // widest level run split (0: the default rule; lp_autotune)
     int br_tail_split = 0;          // a wider level's partial last wave runs split (lp_autotune)
+    int br_pair_max = 0;            // paired-kernel limit as set (0: resident clusters, -1: never)
+    int br_pair_clusters = 0;       // clusters of the paired kernel resident at once
     int ks_slice_max = 0;           // key switches of at most this many batches run sliced (0: rule)
     int executor = LP_EXEC_LEVELS;  // circuits: per-level kernels or the persistent executor
     void *blas = nullptr;           // cuBLAS handle, created on first use
@@ -66,6 +68,13 @@ int ctx_check_err(lp_ctx *c);
 int abar_stride(const lp_ctx *c);
 int ensure_scratch(lp_ctx *c, size_t br_jobs);
 int run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);
+// The blind-rotation kernel choice (BR_VARIANT_*) of an NTT engine selection.
+int br_variant(const lp_ctx *c);
+// Widest level (or remainder) that runs on the paired kernel; 0 = none.
+inline int br_pair_limit(const lp_ctx *c)
+{
+    return c->br_pair_max == 0 ? c->br_pair_clusters : c->br_pair_max < 0 ? 0 : c->br_pair_max;
+}
 int run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);
 int run_br_tensor(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);
 int run_ks_tensor(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);

@@ -37,7 +37,7 @@ EXPORTS = [
     "lp_plan_locpir_known", "lp_circuit_info", "lp_autotune_cached", "lp_set_tuning", "lp_get_tuning",
     "lp_set_executor", "lp_selftest_exec_timeout",
 ]
-LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT = 0, 1, 2, 3, 4
+LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT, LP_BR_NTT_PAIR = 0, 1, 2, 3, 4, 5
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
 LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
 LP_EXEC_LEVELS, LP_EXEC_PERSISTENT = 0, 1
@@ -72,7 +72,7 @@ class lp_circuit_stats(ctypes.Structure):
 
 
 class lp_tuning(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int) for k in ("split_max", "tail_split", "ks_slice_max", "from_cache")]
+    _fields_ = [(k, ctypes.c_int) for k in ("split_max", "tail_split", "ks_slice_max", "from_cache", "pair_max")]
 
 
 class LocpirError(RuntimeError):
@@ -412,8 +412,8 @@ class Context:
         _check(lib().lp_autotune_cached(self.h, path, int(force), ctypes.byref(t)), "lp_autotune_cached")
         return {k: getattr(t, k) for k, _ in lp_tuning._fields_}
 
-    def lp_set_tuning(self, split_max: int = 0, tail_split: int = 0, ks_slice_max: int = 0) -> None:
-        t = lp_tuning(split_max, tail_split, ks_slice_max, 0)
+    def lp_set_tuning(self, split_max: int = 0, tail_split: int = 0, ks_slice_max: int = 0, pair_max: int = 0) -> None:
+        t = lp_tuning(split_max, tail_split, ks_slice_max, 0, pair_max)
         _check(lib().lp_set_tuning(self.h, ctypes.byref(t)), "lp_set_tuning")
 
     def lp_selftest_exec_timeout(self, stream=None) -> None:

@@ -73,7 +73,7 @@ def test_lambda80_dimension_matches_oracle():
 @pytest.mark.parametrize("n", [1, 7, 639])
 def test_lwe_dimension_edges_match_oracle(n):
     """The smallest, an odd and the largest supported LWE dimension (n + 1 = 640 words fills
-    the key switch's 20 words per lane exactly), on both blind-rotation kernels."""
+    the key switch's 20 words per lane exactly), on each blind-rotation kernel."""
     from paper_2407_19871_gb300 import locpir
     p = synth.Params(n=n)
     kn = oracle.keygen(synth.key_draws(6, p))
@@ -89,7 +89,7 @@ def test_lwe_dimension_edges_match_oracle(n):
                    for k, X in enumerate((A, B, Cb)))
         for op in (oracle.AND, oracle.MUX):
             want = oracle.gate_batch(kn, op, a, b, c if op == oracle.MUX else None)
-            for variant in (locpir.LP_BR_NTT_BATCHED, locpir.LP_BR_NTT_SPLIT):
+            for variant in (locpir.LP_BR_NTT_BATCHED, locpir.LP_BR_NTT_SPLIT, locpir.LP_BR_NTT_PAIR):
                 ctx.lp_set_engines(variant, 0)
                 out = empty_dev(cnt, p.n + 1)
                 ctx.lp_gate_batch(op, to_dev(a), to_dev(b), to_dev(c) if op == oracle.MUX else None, out, cnt)
