@@ -500,6 +500,78 @@ __device__ __forceinline__ void ntt_inv_2warp(uint32_t (&y)[16], int h, int lane
     }
 }
 
+// Forward transform of one polynomial by two warps (the mirror of ntt_inv_2warp).  Warp h holds
+// the layout-A registers k = 2 i + h (i < 16), values in [0, 2p).  Stages 0..3 pair registers of
+// the same parity, inside the warp; stage 4 pairs 2 i with 2 i + 1 across the warps, which swap
+// 8 values per lane through X (512 words) and compute its butterflies i < 8 (warp 0) and i >= 8
+// (warp 1), leaving warp h with registers 16 h .. 16 h + 15.  The layout A -> B transpose goes
+// through TB (32 x 33 words, written by both warps), after which warp h holds the layout-B
+// registers k' = 2 i + h: stages 5..8 are local and stage 9 crosses as stage 4 did.  The warps
+// meet at named barrier bar_id (64 threads).  On return y[m], in [0, 22p), is layout-B register
+// 16 h + m; TB and X are free for the caller once both warps have returned.
+__device__ __forceinline__ void ntt_fwd_2warp(uint32_t (&y)[16], int h, int lane, int pi, const PrimeK &K,
+                                              const uint2 *twf, uint32_t *TB, uint32_t *X, int bar_id)
+{
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const int D2 = 8 >> s;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            if (i & D2) continue;
+            const uint2 z = c_tw[pi][0][(1 << s) + (i >> (4 - s))];
+            bfly_fwd(y[i], y[i + D2], z.x, z.y, K);
+        }
+    }
+    uint32_t *out = X + h * 256;
+    const uint32_t *in = X + (1 - h) * 256;
+    uint32_t t[16];
+    // Stage 4: butterfly ii pairs register 2 ii (warp 0's y[ii]) with 2 ii + 1 (warp 1's y[ii]).
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i * 32 + lane] = h == 0 ? y[8 + i] : y[i];
+    bar_red_or(bar_id, 64, false);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint2 z = c_tw[pi][0][16 + 8 * h + i];
+        uint32_t a = h == 0 ? y[i] : in[i * 32 + lane];
+        uint32_t b = h == 0 ? in[i * 32 + lane] : y[8 + i];
+        bfly_fwd(a, b, z.x, z.y, K);
+        t[2 * i] = a;
+        t[2 * i + 1] = b;
+    }
+    // Layout A -> B: registers 16 h + m of layout A in, registers 2 i + h of layout B out.
+#pragma unroll
+    for (int m = 0; m < 16; m++) TB[(16 * h + m) * 33 + lane] = t[m];
+    bar_red_or(bar_id, 64, false);
+#pragma unroll
+    for (int i = 0; i < 16; i++) y[i] = TB[lane * 33 + 2 * i + h];
+#pragma unroll
+    for (int s = 5; s < 9; s++) {
+        const int L = 16 >> (s - 5), L2 = L / 2;
+        const int base = (1 << (s - 5)) - 1;
+#pragma unroll
+        for (int b = 0; b < 16 / L; b++) {
+            const uint2 z = twf[(base + b) * 32 + lane];
+#pragma unroll
+            for (int o = 0; o < L2; o++) bfly_fwd(y[b * L + o], y[b * L + o + L2], z.x, z.y, K);
+        }
+    }
+    // Stage 9, split as stage 4.  X was last read before the transpose's barrier.
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i * 32 + lane] = h == 0 ? y[8 + i] : y[i];
+    bar_red_or(bar_id, 64, false);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint2 z = twf[(15 + 8 * h + i) * 32 + lane];
+        uint32_t a = h == 0 ? y[i] : in[i * 32 + lane];
+        uint32_t b = h == 0 ? in[i * 32 + lane] : y[8 + i];
+        bfly_fwd(a, b, z.x, z.y, K);
+        t[2 * i] = a;
+        t[2 * i + 1] = b;
+    }
+#pragma unroll
+    for (int m = 0; m < 16; m++) y[m] = t[m];
+}
+
 // Sums are stored in transform (layout B) order, index 32 lane + k swizzled to
 // 32 lane + (k ^ lane) so that a warp's 32 lanes hit 32 different banks.
 __device__ __forceinline__ int split_pos(int lane, int k) { return lane * 32 + (k ^ lane); }
@@ -652,10 +724,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
 // ---------------------------------------------------------------------------------
 // Paired split blind rotation: one ciphertext per cluster of two CTAs on two SMs, for levels
 // of at most one ciphertext per two SMs.  CTA rank q of the cluster computes modulo NTT prime
-// q only, on 6 warps: warp r rotates, decomposes and forward-transforms digit row r and parks
-// it (as in br_split_kernel); warps (mc, mh) < 4 sum the six rows' products with the key rows
-// of output component mc for half mh of the registers (64-bit sums, one reduction each) and
-// inverse-transform component mc together (ntt_inv_2warp).  Each CTA writes its residues of
+// q only, on 12 warps: warps 2 r and 2 r + 1 rotate and decompose digit row r (16 coefficients
+// per lane each), forward-transform it together (ntt_fwd_2warp) and park it; warps (mc, mh) < 4
+// sum the six rows' products with the key rows of output component mc for half mh of the
+// registers (64-bit sums, one reduction each) and inverse-transform component mc together
+// (ntt_inv_2warp).  Each CTA writes its residues of
 // both components into its own shared memory and, with st.async, into its partner's, so that
 // after one exchange per step both CTAs hold all four residue polynomials and each recombines
 // both components (centred CRT) into its own copy of ACC; the two copies stay equal.
@@ -672,7 +745,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
 // are initialised before the first st.async) and at exit (no CTA leaves while its partner may
 // still write to it), both reached unconditionally.
 // ---------------------------------------------------------------------------------
-constexpr int PAIR_WARPS = ROWS;
+constexpr int PAIR_WARPS = 2 * ROWS;
 constexpr int PAIR_THREADS = PAIR_WARPS * 32;
 constexpr uint64_t PAIR_XCHG_LIMIT_NS = 4 * WAIT_LIMIT_NS;
 constexpr uint32_t PAIR_XCHG_BYTES = 2u * RING_N * 4u + 4u;   // both components + status word
@@ -680,6 +753,7 @@ constexpr uint32_t PAIR_XCHG_BYTES = 2u * RING_N * 4u + 4u;   // both components
 struct __align__(16) PairSmem {
     uint32_t key[ROWS][CHUNK_WORDS];                     // 48 KB: this step's rows for this CTA's prime
     uint32_t tbuf[ROWS][32 * 33];                         // 24.8 KB: transposes, then the parked rows
+    uint32_t xbuf[ROWS][512];                             // 12 KB: the forward pairs' cross-warp swaps
     uint2 tw[2][LANE_TW * 32];                            // 15.5 KB [dir] for this CTA's prime
     uint32_t res[2][2][2][RING_N];                        // 32 KB [exchange set][prime][component]
     uint32_t acc[2][RING_N];                              // 8 KB
@@ -755,7 +829,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pi = (int)cluster_ctarank();   // this CTA's prime
     const uint32_t peer = 1u - (uint32_t)pi;
-    const int r = warp, c_in = r / LG, p_dig = r % LG;
+    const int r = warp >> 1, fh = warp & 1;   // forward: digit row r, half fh of its registers
+    const int c_in = r / LG, p_dig = r % LG;
     const int n = a.n;
     const PrimeK K = prime_k(pi);
     const int mc = warp >> 1, mh = warp & 1;   // warps 0..3 after the forward transforms
@@ -775,10 +850,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
     __syncthreads();
     hw_cluster_sync();   // both CTAs' barriers are initialised
 
-    uint32_t *tbuf = sm.tbuf[warp];
     uint32_t phase = 0;        // completed uses of this warp's key barrier
     uint32_t xs = 0;           // exchanges done
-    bool pending = false;      // a copy into this warp's key buffer is in flight
+    bool pending = false;      // a copy into this row's key buffer is in flight
     bool aborted = false;
     const int clusters = (int)(gridDim.x >> 1);
     for (int job = (int)(blockIdx.x >> 1); job < a.jobs && !aborted; job += clusters) {
@@ -792,8 +866,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
             sm.acc[1][j] = (e & RING_N) ? (0u - a.mu) : a.mu;
         }
         if (n > 0) {
-            if (lane == 0) pair_issue(sm, a.bsk_hat, pi, r, 0);
-            pending = true;
+            if (lane == 0 && fh == 0) pair_issue(sm, a.bsk_hat, pi, r, 0);
+            pending = true;   // both warps of the row track its barrier
         }
         __syncthreads();
         for (int i = 0; i < n; i++) {
@@ -810,24 +884,27 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
                 }
             }
             if (!ok && lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
-            if (ab != 0 && ok) {
+            // The two warps of a row agree before their transform meets at its barriers.
+            const bool row_ok = !bar_red_or(1 + r, 64, !ok);
+            if (ab != 0 && row_ok) {
                 const uint32_t *A = sm.acc[c_in];
                 const int sh = 32 - BGBIT * (p_dig + 1);
-                uint32_t x[32];
+                uint32_t x[16];
 #pragma unroll
-                for (int k = 0; k < 32; k++) {
-                    const int j = lane + 32 * k;
+                for (int k = 0; k < 16; k++) {
+                    const int j = lane + 32 * (2 * k + fh);   // layout-A register 2 k + fh
                     const int idx = (j - ab) & (2 * RING_N - 1);
                     uint32_t v = A[idx & (RING_N - 1)];
                     v = (idx & RING_N) ? (0u - v) : v;
                     const uint32_t u = v - A[j] + GADGET_OFF;
                     x[k] = ((u >> sh) & 1023u) + (K.p - 512u);
                 }
-                ntt_fwd<false>(x, tbuf, sm.tw[0], lane, pi, K);
+                ntt_fwd_2warp(x, fh, lane, pi, K, sm.tw[0], sm.tbuf[r], sm.xbuf[r], 1 + r);
+                // Park the row: layout-B register k of lane t at [k][t].
 #pragma unroll
-                for (int k = 0; k < 32; k++) tbuf[k * 33 + lane] = x[k];
+                for (int m = 0; m < 16; m++) sm.tbuf[r][(16 * fh + m) * 33 + lane] = x[m];
             }
-            const bool bad = __syncthreads_or(!ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
+            const bool bad = __syncthreads_or(!row_ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
             const bool work = !bad && ab != 0;
             uint32_t ys[16];
 #pragma unroll
@@ -855,7 +932,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
             }
             __syncthreads();
             // Refill this warp's key buffer with the next step's row (every read of it is done).
-            if (!bad && lane == 0 && i + 1 < n) {
+            if (!bad && lane == 0 && fh == 0 && i + 1 < n) {
                 fence_proxy_async_smem();
                 pair_issue(sm, a.bsk_hat, pi, r, i + 1);
             }
@@ -863,7 +940,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
             if (warp < 4) {
                 // Component mc modulo this CTA's prime by warps (mc, 0) and (mc, 1), through the
                 // transpose buffers of rows 2 mc and 2 mc + 1 (all parked rows are read).
-                if (work) ntt_inv_2warp(ys, mh, lane, pi, K, sm.tw[1], sm.tbuf[2 * mc], sm.tbuf[2 * mc + 1], 1 + mc);
+                if (work)
+                    ntt_inv_2warp(ys, mh, lane, pi, K, sm.tw[1], sm.tbuf[2 * mc], sm.tbuf[2 * mc + 1], 1 + ROWS + mc);
                 const int off = ((set * 2 + pi) * 2 + mc) * RING_N;
                 uint32_t *dst = &sm.res[0][0][0][0] + off;
                 const uint32_t rdst = peer_res + 4u * (uint32_t)off;
