@@ -423,6 +423,13 @@ int lp_selftest_wait_timeout(lp_ctx *ctx, uint32_t limit_ms, void *stream);
  * leaving at once, so the others' grid-barrier wait runs out after 2 s; synchronous.  The
  * device error word then holds LP_ETIMEOUT (lp_sync returns it) and the context stays usable. */
 int lp_selftest_exec_timeout(lp_ctx *ctx, void *stream);
+/* lp_selftest_pair_timeout: runs the paired blind rotation on one ciphertext with CTA rank 1 of
+ * its cluster issuing no key copy.  Its first key wait gives up after 2 s, it tells its
+ * partner through the residue exchange's status word, and both CTAs stop after that exchange
+ * (the partner's exchange wait would itself give up after 8 s); synchronous, about 4 s.  The
+ * device error word then holds LP_ETIMEOUT (lp_sync returns it) and the context stays usable.
+ * LP_ENOKEY before lp_load_bsk. */
+int lp_selftest_pair_timeout(lp_ctx *ctx, void *stream);
 
 #ifdef __cplusplus
 }

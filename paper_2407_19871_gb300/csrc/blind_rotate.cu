@@ -822,7 +822,8 @@ __device__ __forceinline__ void pair_issue(PairSmem &sm, const uint32_t *bsk_hat
     bulk_copy_g2s(sm.key[r], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + r) * CHUNK_WORDS, CHUNK_BYTES, &sm.bar[r]);
 }
 
-__global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
+// selftest_stall (self-test only): CTA rank 1 issues no key copy, so its first wait runs out.
+__global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a, int selftest_stall)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PairSmem &sm = *reinterpret_cast<PairSmem *>(smem_raw);
@@ -866,7 +867,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a)
             sm.acc[1][j] = (e & RING_N) ? (0u - a.mu) : a.mu;
         }
         if (n > 0) {
-            if (lane == 0 && fh == 0) pair_issue(sm, a.bsk_hat, pi, r, 0);
+            // (In the stop self-test CTA 1 issues nothing, so its first key wait runs out.)
+            if (lane == 0 && fh == 0 && !(selftest_stall && pi == 1)) pair_issue(sm, a.bsk_hat, pi, r, 0);
             pending = true;   // both warps of the row track its barrier
         }
         __syncthreads();
@@ -1299,14 +1301,21 @@ int br_pair_clusters(int num_sms)
     return n;
 }
 
-static cudaError_t launch_pair(const BrArgs &a, int num_sms, cudaStream_t st)
+static cudaError_t launch_pair(const BrArgs &a, int num_sms, cudaStream_t st, int selftest_stall = 0)
 {
     const int clusters = a.jobs < num_sms / 2 ? a.jobs : num_sms / 2;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     cudaError_t e = pair_config(cfg, attr, clusters, st);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, br_pair_kernel, a);
+    return cudaLaunchKernelEx(&cfg, br_pair_kernel, a, selftest_stall);
+}
+
+cudaError_t launch_pair_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                                 const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st)
+{
+    BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, 1, T_EIGHTH, err};
+    return launch_pair(a, num_sms, st, 1);
 }
 
 // Levels (or remainders) small enough for one CTA or CTA pair per ciphertext: paired when

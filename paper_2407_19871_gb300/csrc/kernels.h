@@ -85,6 +85,11 @@ cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, cons
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms, cudaStream_t st,
                       int variant = BR_VARIANT_AUTO, int split_max = 0, int tail_split = 0, int pair_max = 0,
                       int *launched = nullptr);
+// The paired kernel's stop self-test: one ciphertext (abar: one row), CTA rank 1 of its cluster
+// issues no key copy, so its first wait runs out after 2 s and both CTAs stop after the same
+// exchange with DEV_ERR_TIMEOUT; nothing is in flight when they leave.
+cudaError_t launch_pair_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                                 const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st);
 // Clusters of br_pair_kernel that are resident at once on this device (0 when the query fails).
 int br_pair_clusters(int num_sms);
 size_t br_pair_smem_bytes();

@@ -975,6 +975,27 @@ extern "C" int lp_selftest_exec_timeout(lp_ctx *c, void *stream)
     return e == cudaSuccess ? LP_OK : cuda_fail(e, "executor self-test");
 }
 
+extern "C" int lp_selftest_pair_timeout(lp_ctx *c, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (!c->have_bsk) return fail(LP_ENOKEY, "load the bootstrapping key first");
+    cudaSetDevice(c->device);
+    int rc = ensure_scratch(c, 1);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // One ciphertext whose mod-switched inputs are all 0: every step still waits for its key
+    // rows and exchanges residues.
+    cudaError_t e = cudaMemsetAsync(c->abar.ptr, 0, (size_t)abar_stride(c) * sizeof(uint16_t), st);
+    if (e == cudaSuccess)
+        e = launch_pair_selftest(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
+                                 static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                                 static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n,
+                                 static_cast<int *>(c->err.ptr), c->num_sms, st);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "paired-kernel self-test");
+}
+
 extern "C" int lp_selftest_wait_timeout(lp_ctx *c, uint32_t limit_ms, void *stream)
 {
     if (!c) return fail(LP_EINVAL, "null context");

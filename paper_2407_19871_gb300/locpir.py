@@ -35,7 +35,7 @@ EXPORTS = [
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
     "lp_plan_locpir_known", "lp_circuit_info", "lp_autotune_cached", "lp_set_tuning", "lp_get_tuning",
-    "lp_set_executor", "lp_selftest_exec_timeout",
+    "lp_set_executor", "lp_selftest_exec_timeout", "lp_selftest_pair_timeout",
 ]
 LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT, LP_BR_NTT_PAIR = 0, 1, 2, 3, 4, 5
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
@@ -149,6 +149,7 @@ def lib() -> ctypes.CDLL:
             "lp_set_tuning": (i, [vp, ctypes.POINTER(lp_tuning)]),
             "lp_set_executor": (i, [vp, i]),
             "lp_selftest_exec_timeout": (i, [vp, vp]),
+            "lp_selftest_pair_timeout": (i, [vp, vp]),
             "lp_get_tuning": (i, [vp, ctypes.POINTER(lp_tuning)]),
             "lp_circuit_info": (i, [i, i, i, i, i, vp, ctypes.POINTER(lp_circuit_stats)]),
         }
@@ -418,6 +419,9 @@ class Context:
 
     def lp_selftest_exec_timeout(self, stream=None) -> None:
         _check(lib().lp_selftest_exec_timeout(self.h, _stream(stream)), "lp_selftest_exec_timeout")
+
+    def lp_selftest_pair_timeout(self, stream=None) -> None:
+        _check(lib().lp_selftest_pair_timeout(self.h, _stream(stream)), "lp_selftest_pair_timeout")
 
     def lp_set_executor(self, executor: int) -> None:
         _check(lib().lp_set_executor(self.h, executor), "lp_set_executor")

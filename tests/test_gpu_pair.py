@@ -80,3 +80,16 @@ def test_default_policy_pairs_narrow_levels(engine_ctx, keys):
     assert engine_ctx.lp_get_tuning()["pair_max"] >= -1
     lwe = _random_lwes(331, 3, keys.params.n)
     assert_same(_extract(engine_ctx, LP_BR_NTT, lwe), _extract(engine_ctx, LP_BR_NTT_BATCHED, lwe), "auto vs batched")
+
+
+def test_pair_stop_protocol_times_out_cleanly(engine_ctx, keys):
+    """One CTA of a cluster never gets its first key rows: its wait gives up after 2 s, it passes
+    its stop decision to the partner in the residue exchange, both leave after that exchange and
+    the call reports LP_ETIMEOUT.  The context then bootstraps normally (oracle parity)."""
+    from paper_2407_19871_gb300.locpir import LP_BR_NTT_PAIR, LP_ETIMEOUT, LocpirError
+    engine_ctx.lp_selftest_pair_timeout()
+    with pytest.raises(LocpirError) as e:
+        engine_ctx.lp_sync()
+    assert e.value.code == LP_ETIMEOUT
+    lwe = _random_lwes(341, 2, keys.params.n)
+    assert_same(_extract(engine_ctx, LP_BR_NTT_PAIR, lwe), oracle.bootstrap_extract(keys, lwe), "paired after the stop")
