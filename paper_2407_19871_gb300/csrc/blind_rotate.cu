@@ -728,10 +728,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) br_split_kernel(BrArgs a)
 // per lane each), forward-transform it together (ntt_fwd_2warp) and park it; warps (mc, mh) < 4
 // sum the six rows' products with the key rows of output component mc for half mh of the
 // registers (64-bit sums, one reduction each) and inverse-transform component mc together
-// (ntt_inv_2warp).  Each CTA writes its residues of
-// both components into its own shared memory and, with st.async, into its partner's, so that
-// after one exchange per step both CTAs hold all four residue polynomials and each recombines
-// both components (centred CRT) into its own copy of ACC; the two copies stay equal.
+// (ntt_inv_2warp).  Each CTA writes its residues of both components into its own shared memory
+// and, with st.async, into its partner's, so that after one exchange per step both CTAs hold
+// all four residue polynomials and each recombines both components (centred CRT) into its own
+// copy of ACC; the two copies stay equal.
 //
 // Exchange s lands in buffer set s & 1 and completes on the receiver's mbarrier xbar[s & 1]:
 // the receiver arms it once per exchange (one arrival, PAIR_XCHG_BYTES expected), and every
