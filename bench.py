@@ -382,8 +382,9 @@ def engines_bench(count: int, ks_count: int) -> None:
 
 def br_latency_bench() -> None:
     """Blind-rotation time per launch against the level width, for the batched kernel (4
-    ciphertexts per CTA), the split kernel (one ciphertext per CTA over 12 warps) and the paired
-    kernel (one ciphertext per cluster of two CTAs, one per NTT prime): CUDA
+    ciphertexts per CTA), the split kernel (one ciphertext per CTA over 12 warps), the paired
+    kernel (one ciphertext per cluster of two CTAs, one per NTT prime) and the quad kernel (four
+    CTAs: prime x ACC component): CUDA
     events around the library's blind-rotation launches, median of 3 after a warm-up, outputs
     decrypted.  One JSON line per (kernel, width)."""
     from paper_2407_19871_gb300 import locpir
@@ -392,7 +393,7 @@ def br_latency_bench() -> None:
     ctx, p, s_dev, (A, B), (a, b) = setup_gpu(0, count=max(widths))
     out = torch.empty_like(a)
     for eng, name in ((locpir.LP_BR_NTT_BATCHED, "batched"), (locpir.LP_BR_NTT_SPLIT, "split"),
-                      (locpir.LP_BR_NTT_PAIR, "pair")):
+                      (locpir.LP_BR_NTT_PAIR, "pair"), (locpir.LP_BR_NTT_QUAD, "quad")):
         ctx.lp_set_engines(eng, 0)
         for w in widths:
             ctx.lp_gate_batch(locpir.LP_NAND, a[:w], b[:w], None, out[:w], w)

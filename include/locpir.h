@@ -230,14 +230,17 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
  * lp_bootstrap_extract and lp_key_switch (circuits, plans and the server always use the
  * defaults).  Every engine computes the same exact integers, so outputs are bit-identical.
  *   LP_BR_NTT          two-prime NTT external products in shared memory (default): a level
- *                      of at most one ciphertext per two SMs runs paired (one ciphertext per
- *                      cluster of two CTAs, one per prime, exchanging residues through
- *                      distributed shared memory), one of at most two ciphertexts per SM split
- *                      (one ciphertext per CTA, its 12 digit-and-prime transforms on 12 warps),
- *                      a larger one batched (4 ciphertexts per CTA sharing each key row);
+ *                      of at most one ciphertext per four SMs runs on the quad kernel (one
+ *                      ciphertext per cluster of four CTAs: prime x ACC component, exchanging
+ *                      partial sums and residues through distributed shared memory), one of at
+ *                      most one per two SMs paired (clusters of two CTAs, one per prime), one
+ *                      of at most two per SM split (one ciphertext per CTA, its 12
+ *                      digit-and-prime transforms on 12 warps), a larger one batched (4
+ *                      ciphertexts per CTA sharing each key row);
  *   LP_BR_NTT_BATCHED  the NTT engine, always batched;
  *   LP_BR_NTT_SPLIT    the NTT engine, always split (one CTA per ciphertext);
  *   LP_BR_NTT_PAIR     the NTT engine, always paired;
+ *   LP_BR_NTT_QUAD     the NTT engine, always on the quad kernel;
  *   LP_BR_TENSOR_BF16  per step one Toeplitz(BSK_i) x digit-matrix GEMM on the bf16 tensor
  *                      cores (cuBLAS), factors split into 6-bit limbs so fp32 sums stay exact;
  *   LP_BR_TENSOR_INT8  the same with 8-bit limbs on the int8 tensor cores, int32 sums;
@@ -251,6 +254,7 @@ int lp_locpir_known_batch(lp_ctx *ctx, const lp_query_known *q, size_t nq, void 
 #define LP_BR_NTT_BATCHED 3
 #define LP_BR_NTT_SPLIT 4
 #define LP_BR_NTT_PAIR 5
+#define LP_BR_NTT_QUAD 6
 #define LP_KS_TABLE 0
 #define LP_KS_TENSOR_INT8 1
 int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
@@ -268,11 +272,12 @@ int lp_set_engines(lp_ctx *ctx, int br_engine, int ks_engine);
  *   pair_max      a level (or partial last wave) that would run split and has at most this many
  *                 ciphertexts runs on the paired kernel (one ciphertext per two SMs); 0 = the
  *                 built-in rule (as many as clusters of two CTAs fit on the device at once),
- *                 -1 = never.
+ *                 -1 = never;
+ *   quad_max      the same for the quad kernel (one ciphertext per four SMs), checked first.
  * Every policy gives the same output bits. */
-#define LP_TUNING_SCHEMA 2
+#define LP_TUNING_SCHEMA 3
 typedef struct lp_tuning {
-    int split_max, tail_split, ks_slice_max, from_cache, pair_max;
+    int split_max, tail_split, ks_slice_max, from_cache, pair_max, quad_max;
 } lp_tuning;
 
 /* lp_autotune: measures the policy on this device (synthetic inputs, CUDA events, about 0.5 s):
@@ -280,9 +285,10 @@ typedef struct lp_tuning {
  * multiple of the SM count up to which the split kernel is still faster, never below one per
  * SM; tail_split when the split kernel beats a batched wave at one per SM), and the key switch
  * sliced against whole-table CTAs at 1/4 to 1 batch per SM (ks_slice_max: the widest batch
- * count of the leading run where slicing is faster), and the paired kernel against the split
+ * count of the leading run where slicing is faster), the paired kernel against the split
  * kernel at one ciphertext per resident cluster (pair_max: that count when paired is faster,
- * else -1).  Applies it to the context.
+ * else -1), and the quad kernel against the faster of those two at one ciphertext per
+ * resident cluster of four (quad_max, likewise).  Applies it to the context.
  * *split_max_out (may be NULL) receives split_max.  Needs both keys (LP_ENOKEY); uses the
  * context's scratch, so call it while no other work of this context is in flight (not while a
  * server runs). */
@@ -430,6 +436,11 @@ int lp_selftest_exec_timeout(lp_ctx *ctx, void *stream);
  * device error word then holds LP_ETIMEOUT (lp_sync returns it) and the context stays usable.
  * LP_ENOKEY before lp_load_bsk. */
 int lp_selftest_pair_timeout(lp_ctx *ctx, void *stream);
+/* lp_selftest_quad_timeout: the same for the quad blind rotation (a cluster of four CTAs; rank 1
+ * issues no key copy).  Its stop decision reaches the CTA of the same prime in the partial-sum
+ * exchange and the other prime's CTAs in the residue exchange of the same step, so all four
+ * stop together; synchronous, about 4 s; LP_ETIMEOUT afterwards, the context stays usable. */
+int lp_selftest_quad_timeout(lp_ctx *ctx, void *stream);
 
 #ifdef __cplusplus
 }

@@ -572,6 +572,147 @@ __device__ __forceinline__ void ntt_fwd_2warp(uint32_t (&y)[16], int h, int lane
     for (int m = 0; m < 16; m++) y[m] = t[m];
 }
 
+// One stage of a four-warp transform whose pairs cross two warps (this one, w, and `partner`):
+// each holds 8 values, the low-side warp (low) the pairs' first operands; they swap 4 values per
+// lane through R (4 warps x 128 words) and compute 4 butterflies each, the low side the pairs
+// of its registers 0..3, with twiddle z[j] for its butterfly j.  On return registers 0..3 hold
+// the pairs' first outputs, 4..7 the second.
+template <bool Fwd>
+__device__ __forceinline__ void cross4(uint32_t (&y)[8], int w, int partner, bool low, int lane, const uint2 (&z)[4],
+                                       const PrimeK &K, uint32_t *R, int bar_id)
+{
+    uint32_t *out = R + w * 128;
+    const uint32_t *in = R + partner * 128;
+#pragma unroll
+    for (int j = 0; j < 4; j++) out[j * 32 + lane] = low ? y[4 + j] : y[j];
+    bar_red_or(bar_id, 128, false);
+    uint32_t t[8];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        uint32_t a = low ? y[j] : in[j * 32 + lane];
+        uint32_t b = low ? in[j * 32 + lane] : y[4 + j];
+        if (Fwd)
+            bfly_fwd(a, b, z[j].x, z[j].y, K);
+        else
+            bfly_inv(a, b, z[j].x, z[j].y, K);
+        t[j] = a;
+        t[4 + j] = b;
+    }
+#pragma unroll
+    for (int m = 0; m < 8; m++) y[m] = t[m];
+}
+
+// Forward transform of one polynomial by four warps.  Warp w = 2 hb + w0 holds the layout-A
+// registers 4 i + w (i < 8), values in [0, 2p).  Stages 0..2 are local; stage 3 (pairs k, k + 2)
+// crosses warps w and w ^ 2 and stage 4 (k, k + 1) warps w and w ^ 1 (cross4, each through its
+// own half of X, 1024 words), after which warp w holds registers 16 hb + 4 j + 2 w0 + e at
+// y[4 e + j].  The layout A -> B transpose goes through TB (32 x 33 words, all four warps),
+// giving warp w the layout-B registers 4 i + w; stages 5..7 are local and stages 8 and 9 cross
+// as 3 and 4 did.  The warps meet at named barrier bar_id (128 threads).  On return y[4 e + j],
+// in [0, 22p), is layout-B register 16 hb + 4 j + 2 w0 + e; TB and X are free for the caller
+// once all four warps have returned.
+__device__ __forceinline__ void ntt_fwd_4warp(uint32_t (&y)[8], int w, int lane, int pi, const PrimeK &K,
+                                              const uint2 *twf, uint32_t *TB, uint32_t *X, int bar_id)
+{
+    const int hb = w >> 1, w0 = w & 1;
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        const int D4 = 4 >> s;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if (i & D4) continue;
+            const uint2 z = c_tw[pi][0][(1 << s) + (i >> (3 - s))];
+            bfly_fwd(y[i], y[i + D4], z.x, z.y, K);
+        }
+    }
+    uint2 z[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = c_tw[pi][0][8 + 4 * hb + j];
+    cross4<true>(y, w, w ^ 2, hb == 0, lane, z, K, X, bar_id);
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = c_tw[pi][0][16 + 8 * hb + 2 * j + w0];
+    cross4<true>(y, w, w ^ 1, w0 == 0, lane, z, K, X + 512, bar_id);
+#pragma unroll
+    for (int e = 0; e < 2; e++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) TB[(16 * hb + 4 * j + 2 * w0 + e) * 33 + lane] = y[4 * e + j];
+    bar_red_or(bar_id, 128, false);
+#pragma unroll
+    for (int i = 0; i < 8; i++) y[i] = TB[lane * 33 + 4 * i + w];
+#pragma unroll
+    for (int s = 5; s < 8; s++) {
+        const int L = 16 >> (s - 5), L2 = L / 2, L4 = L / 4;
+        const int base = (1 << (s - 5)) - 1;
+#pragma unroll
+        for (int b = 0; b < 8 / L2; b++) {
+            const uint2 zz = twf[(base + b) * 32 + lane];
+#pragma unroll
+            for (int o = 0; o < L4; o++) bfly_fwd(y[b * L2 + o], y[b * L2 + o + L4], zz.x, zz.y, K);
+        }
+    }
+    // Each half of X was last read before the barrier that follows its next writer's barrier.
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = twf[(7 + 4 * hb + j) * 32 + lane];
+    cross4<true>(y, w, w ^ 2, hb == 0, lane, z, K, X, bar_id);
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = twf[(15 + 8 * hb + 2 * j + w0) * 32 + lane];
+    cross4<true>(y, w, w ^ 1, w0 == 0, lane, z, K, X + 512, bar_id);
+}
+
+// Inverse transform of one polynomial by four warps.  Warp w = 2u + v holds layout-B registers
+// 8 w .. 8 w + 7 (bit 4 of the register index is u, bit 3 is v), values in [0, 2p).  Stages
+// 9..7 are local; stage 6 (pairs k, k + 8) crosses warps w and w ^ 1, stage 5 (k, k + 16) warps
+// w and w ^ 2 (cross4, each through its own half of X, 1024 words), after which warp w holds
+// registers 16 c + 8 u + 4 v + j at y[4 c + j].  The layout B -> A transpose goes through TB
+// (32 x 33 words, all four warps), giving warp w the layout-A registers 8 w .. 8 w + 7 again;
+// stages 4..2 are local and stages 1 and 0 cross as 6 and 5 did.  The warps meet at named
+// barrier bar_id (128 threads).  On return y[4 c + j], in [0, 2p), is the natural-order
+// coefficient lane + 32 (16 c + 8 u + 4 v + j).
+__device__ __forceinline__ void ntt_inv_4warp(uint32_t (&y)[8], int w, int lane, int pi, const PrimeK &K,
+                                              const uint2 *twi, uint32_t *TB, uint32_t *X, int bar_id)
+{
+    const int u = w >> 1, v = w & 1;
+#pragma unroll
+    for (int s = 9; s >= 7; s--) {
+        const int L = 16 >> (s - 5);
+        const int base = (1 << (s - 5)) - 1;
+#pragma unroll
+        for (int b = 0; b < 8 / (2 * L); b++) {
+            const uint2 zz = twi[(base + 4 * w / L + b) * 32 + lane];
+#pragma unroll
+            for (int o = 0; o < L; o++) bfly_inv(y[b * 2 * L + o], y[b * 2 * L + o + L], zz.x, zz.y, K);
+        }
+    }
+    uint2 z[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = twi[(1 + u) * 32 + lane];
+    cross4<false>(y, w, w ^ 1, v == 0, lane, z, K, X, bar_id);
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = twi[lane];
+    cross4<false>(y, w, w ^ 2, u == 0, lane, z, K, X + 512, bar_id);
+#pragma unroll
+    for (int m = 0; m < 8; m++) TB[lane * 33 + 16 * (m >> 2) + 8 * u + 4 * v + (m & 3)] = y[m];
+    bar_red_or(bar_id, 128, false);
+#pragma unroll
+    for (int i = 0; i < 8; i++) y[i] = TB[(8 * w + i) * 33 + lane];
+#pragma unroll
+    for (int s = 4; s >= 2; s--) {
+        const int D = 16 >> s;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if (i & D) continue;
+            const uint2 zz = c_tw[pi][1][(1 << s) + ((8 * w + i) >> (5 - s))];
+            bfly_inv(y[i], y[i + D], zz.x, zz.y, K);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = c_tw[pi][1][2 + u];
+    cross4<false>(y, w, w ^ 1, v == 0, lane, z, K, X, bar_id);
+#pragma unroll
+    for (int j = 0; j < 4; j++) z[j] = c_tw[pi][1][1];
+    cross4<false>(y, w, w ^ 2, u == 0, lane, z, K, X + 512, bar_id);
+}
+
 // Sums are stored in transform (layout B) order, index 32 lane + k swizzled to
 // 32 lane + (k ^ lane) so that a warp's 32 lanes hit 32 different banks.
 __device__ __forceinline__ int split_pos(int lane, int k) { return lane * 32 + (k ^ lane); }
@@ -996,6 +1137,250 @@ __global__ void __launch_bounds__(PAIR_THREADS, 1) br_pair_kernel(BrArgs a, int 
 }
 
 // ---------------------------------------------------------------------------------
+// Quad split blind rotation: one ciphertext per cluster of four CTAs on four SMs, for levels
+// of at most one ciphertext per four SMs.  CTA rank 2 g + q computes modulo NTT prime q and
+// owns ACC component g; because digit rows 3 g .. 3 g + 2 decompose component g, it needs no
+// other part of ACC.  On 12 warps:
+//   * warps 4 r' .. 4 r' + 3 decompose digit row 3 g + r' (8 coefficients per lane each),
+//     forward-transform it together (ntt_fwd_4warp) and park it;
+//   * warps 4 mc + w (mc, w < 2, 4) sum the three parked rows' products with the key rows of
+//     output component mc for registers 8 w .. 8 w + 7 (64-bit sums, one reduction each);
+//   * exchange P: the partial sums of component 1 - g go to the CTA of the same prime that owns
+//     it (rank ^ 2), whose partial sums of component g arrive here; warps 4 g .. 4 g + 3 add
+//     them and inverse-transform component g together (ntt_inv_4warp);
+//   * exchange R: the residues of component g modulo this prime go to the CTA of the other
+//     prime that owns the same component (rank ^ 1), whose residues arrive here; all warps
+//     recombine component g (centred CRT) into ACC.
+// Both exchanges work as in br_pair_kernel (st.async stores that count their bytes on the
+// receiver's mbarrier of the exchange's parity, bounded acquire waits, one status word each).
+// A CTA's status in exchange R is its stop decision after exchange P (its own key wait or its
+// P partner's status), so a stop reaches all four CTAs by the end of the same step, and every
+// CTA still sends every byte of both exchanges.  CTA 0 writes the extracted a', CTA 2 b'.
+// ---------------------------------------------------------------------------------
+constexpr int QUAD_ROWS = LG;                          // digit rows per CTA
+constexpr int QUAD_WARPS = 4 * QUAD_ROWS;
+constexpr int QUAD_THREADS = QUAD_WARPS * 32;
+constexpr uint32_t QUAD_XCHG_BYTES = RING_N * 4u + 4u;   // one polynomial + status word
+// Dynamic shared memory of at least this size keeps two CTAs of a cluster off one SM.
+constexpr size_t QUAD_SMEM_MIN = 116 * 1024;
+
+struct __align__(16) QuadSmem {
+    uint32_t key[QUAD_ROWS][CHUNK_WORDS];                 // 24 KB: this step's rows for this prime
+    uint32_t tbuf[QUAD_ROWS][32 * 33];                     // 12.4 KB: transposes, then the parked rows
+    uint32_t xbuf[QUAD_ROWS][1024];                        // 12 KB: the four-warp transforms' swaps
+    uint2 tw[2][LANE_TW * 32];                             // 15.5 KB [dir] for this CTA's prime
+    uint32_t psum[2][RING_N];                              // 8 KB: partner's partial sums, by set
+    uint32_t res[2][2][RING_N];                            // 16 KB [set][prime]: component g residues
+    uint32_t acc[RING_N];                                  // 4 KB: ACC component g
+    uint16_t abar[ABAR_STRIDE_MAX];                        // 2 KB
+    uint64_t bar[QUAD_ROWS];                               // key copies, one per row
+    uint64_t xp[2], xr[2];                                 // exchanges P and R, by set
+    uint32_t status_p[2], status_r[2];                     // the partners' status words, by set
+    int abort;                                             // a key wait of this CTA gave up
+};
+
+size_t br_quad_smem_bytes() { return sizeof(QuadSmem) > QUAD_SMEM_MIN ? sizeof(QuadSmem) : QUAD_SMEM_MIN; }
+
+__device__ __forceinline__ void quad_issue(QuadSmem &sm, const uint32_t *bsk_hat, int pi, int g, int rl, int i)
+{
+    mbar_arrive_expect_tx(&sm.bar[rl], CHUNK_BYTES);
+    bulk_copy_g2s(sm.key[rl], bsk_hat + ((size_t)(i * 2 + pi) * ROWS + LG * g + rl) * CHUNK_WORDS, CHUNK_BYTES,
+                  &sm.bar[rl]);
+}
+
+// selftest_stall (self-test only): CTA rank 1 issues no key copy, so its first wait runs out.
+__global__ void __launch_bounds__(QUAD_THREADS, 1) br_quad_kernel(BrArgs a, int selftest_stall)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    QuadSmem &sm = *reinterpret_cast<QuadSmem *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int pi = (int)(rank & 1u), g = (int)(rank >> 1);   // prime, owned component
+    const int rl = warp >> 2, fw = warp & 3;                   // forward: local row, warp in row
+    const int mc = warp >> 2, mw = warp & 3;                   // products (warps 0..7)
+    const int n = a.n;
+    const PrimeK K = prime_k(pi);
+    const uint32_t half_peer = rank ^ 2u, prime_peer = rank ^ 1u;
+    const uint32_t peer_psum = mapa_shared(&sm.psum[0][0], half_peer);
+    const uint32_t peer_xp = mapa_shared(&sm.xp[0], half_peer);
+    const uint32_t peer_status_p = mapa_shared(&sm.status_p[0], half_peer);
+    const uint32_t peer_res = mapa_shared(&sm.res[0][0][0], prime_peer);
+    const uint32_t peer_xr = mapa_shared(&sm.xr[0], prime_peer);
+    const uint32_t peer_status_r = mapa_shared(&sm.status_r[0], prime_peer);
+
+    for (int i = threadIdx.x; i < 2 * LANE_TW * 32; i += blockDim.x)
+        (&sm.tw[0][0])[i] = a.tw_lane[(size_t)pi * 2 * LANE_TW * 32 + i];
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < QUAD_ROWS; w++) mbar_init(&sm.bar[w], 1);
+        for (int s = 0; s < 2; s++) {
+            mbar_init(&sm.xp[s], 1);
+            mbar_init(&sm.xr[s], 1);
+        }
+        sm.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    hw_cluster_sync();   // all four CTAs' barriers are initialised
+
+    uint32_t phase = 0;        // completed uses of this warp's key barrier
+    uint32_t xs = 0;           // steps exchanged (each step: one P and one R exchange)
+    bool pending = false;      // a copy into this row's key buffer is in flight
+    bool aborted = false;
+    const int clusters = (int)(gridDim.x >> 2);
+    for (int job = (int)(blockIdx.x >> 2); job < a.jobs && !aborted; job += clusters) {
+        const uint16_t *src = a.abar + (size_t)job * a.abar_stride;
+        for (int i = threadIdx.x; i <= n; i += blockDim.x) sm.abar[i] = src[i];
+        __syncthreads();
+        const int bb = sm.abar[n];
+        for (int j = threadIdx.x; j < RING_N; j += blockDim.x) {
+            const int e = (j + bb) & (2 * RING_N - 1);
+            sm.acc[j] = g == 0 ? 0u : ((e & RING_N) ? (0u - a.mu) : a.mu);
+        }
+        if (n > 0) {
+            if (lane == 0 && fw == 0 && !(selftest_stall && rank == 1u)) quad_issue(sm, a.bsk_hat, pi, g, rl, 0);
+            pending = true;   // the row's four warps track its barrier
+        }
+        __syncthreads();
+        for (int i = 0; i < n; i++) {
+            const int ab = sm.abar[i];   // all four CTAs run the same job: the same decisions
+            const int set = (int)(xs & 1u);
+            const uint32_t par = (xs >> 1) & 1u;
+            if (threadIdx.x == 0) {
+                mbar_arrive_expect_tx(&sm.xp[set], QUAD_XCHG_BYTES);
+                mbar_arrive_expect_tx(&sm.xr[set], QUAD_XCHG_BYTES);
+            }
+            bool ok = true;
+            if (pending) {
+                ok = mbar_wait_bounded(&sm.bar[rl], phase & 1u, &sm.abort);
+                if (ok) {
+                    phase++;
+                    pending = false;   // else the copy stays pending for the drain at exit
+                }
+            }
+            if (!ok && lane == 0) *reinterpret_cast<volatile int *>(&sm.abort) = 1;
+            // The four warps of a row agree before their transform meets at its barriers.
+            const bool row_ok = !bar_red_or(1 + rl, 128, !ok);
+            if (ab != 0 && row_ok) {
+                const uint32_t *A = sm.acc;
+                const int sh = 32 - BGBIT * (rl + 1);
+                uint32_t x[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int j = lane + 32 * (4 * k + fw);   // layout-A register 4 k + fw
+                    const int idx = (j - ab) & (2 * RING_N - 1);
+                    uint32_t v = A[idx & (RING_N - 1)];
+                    v = (idx & RING_N) ? (0u - v) : v;
+                    const uint32_t u = v - A[j] + GADGET_OFF;
+                    x[k] = ((u >> sh) & 1023u) + (K.p - 512u);
+                }
+                ntt_fwd_4warp(x, fw, lane, pi, K, sm.tw[0], sm.tbuf[rl], sm.xbuf[rl], 1 + rl);
+                // Park the row: layout-B register k of lane t at [k][t].
+#pragma unroll
+                for (int e = 0; e < 2; e++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        sm.tbuf[rl][(16 * (fw >> 1) + 4 * j + 2 * (fw & 1) + e) * 33 + lane] = x[4 * e + j];
+            }
+            const bool bad = __syncthreads_or(!row_ok || *reinterpret_cast<volatile int *>(&sm.abort) != 0);
+            const bool work = !bad && ab != 0;
+            uint32_t ys[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) ys[t] = 0u;
+            if (work && warp < 8) {
+                // Partial sums of component mc over this CTA's three rows, registers 8 mw + 4 qq + e.
+#pragma unroll
+                for (int qq = 0; qq < 2; qq++) {
+                    const int q = 2 * mw + qq;
+                    unsigned long long s4[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+                    for (int rr = 0; rr < QUAD_ROWS; rr++) {
+                        const uint4 kv = reinterpret_cast<const uint4 *>(sm.key[rr] + mc * RING_N)[q * 32 + lane];
+                        const uint32_t kk[4] = {kv.x, kv.y, kv.z, kv.w};
+                        const uint32_t *xr = sm.tbuf[rr];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) s4[e] += (unsigned long long)xr[(4 * q + e) * 33 + lane] * kk[e];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        uint32_t v = redc64(s4[e], K);
+                        v = umin_u32(v, v - 2u * K.p2);
+                        ys[4 * qq + e] = umin_u32(v, v - K.p2);
+                    }
+                }
+            }
+            __syncthreads();
+            // Refill the key buffers with the next step's rows (every read of them is done).
+            if (!bad && lane == 0 && fw == 0 && i + 1 < n) {
+                fence_proxy_async_smem();
+                quad_issue(sm, a.bsk_hat, pi, g, rl, i + 1);
+            }
+            if (!bad && i + 1 < n) pending = true;
+            bool stop_p = false;   // known to warps 4 g .. 4 g + 3
+            if (warp < 8 && mc != g) {
+                // Exchange P out: component 1 - g to the CTA of this prime that owns it.
+                const uint32_t rdst = peer_psum + 4u * (uint32_t)(set * RING_N);
+                const uint32_t rbar = peer_xp + 8u * (uint32_t)set;
+#pragma unroll
+                for (int t = 0; t < 8; t++) st_async_u32(rdst + 4u * (uint32_t)((8 * mw + t) * 32 + lane), ys[t], rbar);
+                if (mw == 0 && lane == 0) st_async_u32(peer_status_p + 4u * (uint32_t)set, bad ? 1u : 0u, rbar);
+            } else if (warp < 8) {
+                // Exchange P in, then component g modulo this prime: add, inverse-transform, and
+                // exchange R out to the other prime's CTA of this component.
+                const bool arrived = pair_wait_xchg(&sm.xp[set], par);
+                stop_p = bad || !arrived || *reinterpret_cast<volatile uint32_t *>(&sm.status_p[set]) != 0u;
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const uint32_t v = ys[t] + sm.psum[set][(8 * mw + t) * 32 + lane];
+                    ys[t] = umin_u32(v, v - K.p2);
+                }
+                if (work)
+                    ntt_inv_4warp(ys, mw, lane, pi, K, sm.tw[1], sm.tbuf[0], sm.tbuf[1], 1 + QUAD_ROWS);
+                uint32_t *dst = &sm.res[set][pi][0];
+                const uint32_t rdst = peer_res + 4u * (uint32_t)((set * 2 + pi) * RING_N);
+                const uint32_t rbar = peer_xr + 8u * (uint32_t)set;
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int j = lane + 32 * (16 * (t >> 2) + 8 * (mw >> 1) + 4 * (mw & 1) + (t & 3));
+                    const uint32_t v = umin_u32(ys[t], ys[t] - K.p);
+                    dst[j] = v;
+                    st_async_u32(rdst + 4u * (uint32_t)j, v, rbar);
+                }
+                if (mw == 0 && lane == 0) st_async_u32(peer_status_r + 4u * (uint32_t)set, stop_p ? 1u : 0u, rbar);
+            }
+            const bool arrived_r = pair_wait_xchg(&sm.xr[set], par);
+            xs++;
+            const bool stop = __syncthreads_or(stop_p || bad || !arrived_r ||
+                                               *reinterpret_cast<volatile uint32_t *>(&sm.status_r[set]) != 0u);
+            if (stop) {
+                aborted = true;
+                break;
+            }
+            if (ab != 0) {
+                // ACC_g += CRT(residues), from this step's set.
+                for (int j = threadIdx.x; j < RING_N; j += blockDim.x)
+                    sm.acc[j] += crt_lift(sm.res[set][0][j], sm.res[set][1][j]);
+            }
+            __syncthreads();
+        }
+        if (aborted) break;
+        // Sample extraction: CTA 0 (prime 0, component 0) writes a', CTA 2 (component 1) b'.
+        uint32_t *dst = a.ext + (size_t)job * EXT_STRIDE;
+        if (rank == 0u)
+            for (int j = threadIdx.x; j < RING_N; j += blockDim.x)
+                dst[j] = j == 0 ? sm.acc[0] : 0u - sm.acc[RING_N - j];
+        if (rank == 2u && threadIdx.x == 0) dst[RING_N] = sm.acc[0];
+        __syncthreads();
+    }
+    if (aborted && threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    // No bulk copy may still be in flight when the CTA exits (only possible after an abort).
+    if (lane == 0 && pending) {
+        volatile int never = 0;
+        if (!mbar_wait_bounded(&sm.bar[rl], phase & 1u, &never)) atomicOr(a.err, DEV_ERR_TIMEOUT);
+    }
+    hw_cluster_sync();   // no partner writes to this CTA's shared memory any more
+}
+
+// ---------------------------------------------------------------------------------
 // Bootstrapping key -> transform domain.  One warp per (i, prime, row, component)
 // polynomial: centred lift mod p, forward NTT, scale by N^-1 2^32 mod p, store in the
 // chunk layout the blind rotation reads (component c, then [q][lane][4] so that lane t
@@ -1269,23 +1654,35 @@ static cudaError_t launch_split(const BrArgs &a, int num_sms, cudaStream_t st)
     return cudaGetLastError();
 }
 
-static cudaError_t pair_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int clusters, cudaStream_t st)
+// Launch configuration of a cluster kernel: `csize` CTAs per cluster, `clusters` clusters.
+static cudaError_t cluster_config(const void *kernel, int threads, size_t smem, int csize, int clusters,
+                                  cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, cudaStream_t st)
 {
-    const size_t smem = sizeof(PairSmem);
-    cudaError_t e = cudaFuncSetAttribute(br_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cfg = cudaLaunchConfig_t{};
-    cfg.gridDim = dim3((unsigned)(2 * clusters));
-    cfg.blockDim = dim3(PAIR_THREADS);
+    cfg.gridDim = dim3((unsigned)(csize * clusters));
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = (unsigned)csize;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaSuccess;
+}
+
+static cudaError_t pair_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int clusters, cudaStream_t st)
+{
+    return cluster_config((const void *)br_pair_kernel, PAIR_THREADS, sizeof(PairSmem), 2, clusters, cfg, attr, st);
+}
+
+static cudaError_t quad_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr, int clusters, cudaStream_t st)
+{
+    return cluster_config((const void *)br_quad_kernel, QUAD_THREADS, br_quad_smem_bytes(), 4, clusters, cfg, attr,
+                          st);
 }
 
 int br_pair_clusters(int num_sms)
@@ -1301,6 +1698,28 @@ int br_pair_clusters(int num_sms)
     return n;
 }
 
+// Resident clusters of four per device, recorded by br_quad_clusters (the GPCs' SM counts need
+// not be multiples of 4, so fewer than num_sms / 4 may fit at once); launch_quad launches no
+// more clusters than that, so none waits for another to finish.
+constexpr int QUAD_MAX_DEVICES = 64;
+static int g_quad_resident[QUAD_MAX_DEVICES];   // read and written with __atomic builtins
+
+int br_quad_clusters(int num_sms)
+{
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (quad_config(cfg, attr, num_sms / 4, nullptr) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, br_quad_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < QUAD_MAX_DEVICES)
+        __atomic_store_n(&g_quad_resident[dev], n, __ATOMIC_RELAXED);
+    return n;
+}
+
 static cudaError_t launch_pair(const BrArgs &a, int num_sms, cudaStream_t st, int selftest_stall = 0)
 {
     const int clusters = a.jobs < num_sms / 2 ? a.jobs : num_sms / 2;
@@ -1311,6 +1730,21 @@ static cudaError_t launch_pair(const BrArgs &a, int num_sms, cudaStream_t st, in
     return cudaLaunchKernelEx(&cfg, br_pair_kernel, a, selftest_stall);
 }
 
+static cudaError_t launch_quad(const BrArgs &a, int num_sms, cudaStream_t st, int selftest_stall = 0)
+{
+    int cap = num_sms / 4, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < QUAD_MAX_DEVICES) {
+        const int r = __atomic_load_n(&g_quad_resident[dev], __ATOMIC_RELAXED);
+        if (r > 0 && r < cap) cap = r;
+    }
+    const int clusters = a.jobs < cap ? a.jobs : cap;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = quad_config(cfg, attr, clusters, st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, br_quad_kernel, a, selftest_stall);
+}
+
 cudaError_t launch_pair_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                                  const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st)
 {
@@ -1318,10 +1752,18 @@ cudaError_t launch_pair_selftest(const uint16_t *abar, int abar_stride, uint32_t
     return launch_pair(a, num_sms, st, 1);
 }
 
-// Levels (or remainders) small enough for one CTA or CTA pair per ciphertext: paired when
-// they fit pair_max clusters, else split.
-static cudaError_t launch_small(const BrArgs &a, int num_sms, cudaStream_t st, int pair_max)
+cudaError_t launch_quad_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                                 const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st)
 {
+    BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, 1, T_EIGHTH, err};
+    return launch_quad(a, num_sms, st, 1);
+}
+
+// Levels (or remainders) small enough for one CTA, CTA pair or CTA quad per ciphertext: on four
+// SMs when they fit quad_max clusters, on two when they fit pair_max, else split.
+static cudaError_t launch_small(const BrArgs &a, int num_sms, cudaStream_t st, int pair_max, int quad_max)
+{
+    if (a.jobs <= quad_max) return launch_quad(a, num_sms, st);
     return a.jobs <= pair_max ? launch_pair(a, num_sms, st) : launch_split(a, num_sms, st);
 }
 
@@ -1338,26 +1780,28 @@ static cudaError_t launch_batched(const BrArgs &a, int num_sms, cudaStream_t st)
 
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms,
-                      cudaStream_t st, int variant, int split_max, int tail_split, int pair_max, int *launched)
+                      cudaStream_t st, int variant, int split_max, int tail_split, int pair_max, int quad_max,
+                      int *launched)
 {
     if (launched) *launched = 0;
     if (jobs <= 0) return cudaSuccess;
     BrArgs a{abar, ext, bsk_hat, tw_lane, n, abar_stride, jobs, mu, err};
-    if (variant == BR_VARIANT_PAIR) {
+    if (variant == BR_VARIANT_PAIR || variant == BR_VARIANT_QUAD) {
         if (launched) *launched = 1;
-        return launch_pair(a, num_sms, st);
+        return variant == BR_VARIANT_PAIR ? launch_pair(a, num_sms, st) : launch_quad(a, num_sms, st);
     }
     // Policy (measured on GB300): a split CTA finishes one ciphertext in about 4 ms, a batched
     // wave of up to 4 per SM takes 13.3-14.3 ms, so levels of up to two ciphertexts per SM run
     // split (one or two split waves) and larger ones batched, unless lp_autotune measured
-    // another crossing on this device.  Levels that fit pair_max clusters of two SMs run on the
-    // paired kernel instead.
+    // another crossing on this device.  Levels that fit quad_max clusters of four SMs, or
+    // pair_max clusters of two, run on the quad or paired kernel instead.
     const int smax = split_max > 0 ? split_max : 2 * num_sms;
     const int pmax = variant == BR_VARIANT_AUTO ? pair_max : 0;
+    const int qmax = variant == BR_VARIANT_AUTO ? quad_max : 0;
     const bool split = variant == BR_VARIANT_SPLIT || (variant == BR_VARIANT_AUTO && jobs <= smax);
     if (split) {
         if (launched) *launched = 1;
-        return launch_small(a, num_sms, st, pmax);
+        return launch_small(a, num_sms, st, pmax, qmax);
     }
     // A wider level whose last batched wave would be partial: with tail_split (chosen by the
     // autotuner), the full waves run batched and the remainder, when it is within the split
@@ -1371,7 +1815,7 @@ cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, cons
         tail.abar = abar + (size_t)head.jobs * abar_stride;
         tail.ext = ext + (size_t)head.jobs * EXT_STRIDE;
         cudaError_t e = launch_batched(head, num_sms, st);
-        if (e == cudaSuccess) e = launch_small(tail, num_sms, st, pmax);
+        if (e == cudaSuccess) e = launch_small(tail, num_sms, st, pmax, qmax);
         if (launched) *launched = 2;
         return e;
     }

@@ -175,7 +175,7 @@ static int enqueue_schedule(lp_ctx *c, const Schedule &S, const RunBufs &B, cuda
         int launched = 0;
         e = launch_br(B.abar, abar_stride(c), B.ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
                       static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)ps.br_cnt, T_EIGHTH, err, c->num_sms, st,
-                      BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, br_pair_limit(c), &launched);
+                      BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, br_pair_limit(c), br_quad_limit(c), &launched);
         if (timed) timer_end(c, "br", st, ev0);
         c->launches += launched;
         if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");

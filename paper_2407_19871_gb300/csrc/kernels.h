@@ -76,22 +76,29 @@ constexpr int BR_VARIANT_AUTO = 0;
 constexpr int BR_VARIANT_BATCHED = 1;
 constexpr int BR_VARIANT_SPLIT = 2;
 constexpr int BR_VARIANT_PAIR = 3;
+constexpr int BR_VARIANT_QUAD = 4;
 // tail_split: with AUTO, a level wider than split_max runs its full batched waves batched and
 // the remainder split when the remainder is at most split_max.  pair_max: with AUTO, a level (or
 // remainder) run split that has at most pair_max ciphertexts runs on br_pair_kernel instead
-// (one ciphertext per cluster of two CTAs, one per prime); 0 never.  *launched (may be null)
+// (one ciphertext per cluster of two CTAs, one per prime), and one of at most quad_max on
+// br_quad_kernel (four CTAs: prime x ACC component); 0 never.  *launched (may be null)
 // receives the number of kernels launched.
 cudaError_t launch_br(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                       const uint2 *tw_lane, int n, int jobs, uint32_t mu, int *err, int num_sms, cudaStream_t st,
                       int variant = BR_VARIANT_AUTO, int split_max = 0, int tail_split = 0, int pair_max = 0,
-                      int *launched = nullptr);
+                      int quad_max = 0, int *launched = nullptr);
 // The paired kernel's stop self-test: one ciphertext (abar: one row), CTA rank 1 of its cluster
 // issues no key copy, so its first wait runs out after 2 s and both CTAs stop after the same
 // exchange with DEV_ERR_TIMEOUT; nothing is in flight when they leave.
 cudaError_t launch_pair_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
                                  const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st);
+// The same for the quad kernel (CTA rank 1 of its cluster of four issues no key copy).
+cudaError_t launch_quad_selftest(const uint16_t *abar, int abar_stride, uint32_t *ext, const uint32_t *bsk_hat,
+                                 const uint2 *tw_lane, int n, int *err, int num_sms, cudaStream_t st);
 // Clusters of br_pair_kernel that are resident at once on this device (0 when the query fails).
 int br_pair_clusters(int num_sms);
+int br_quad_clusters(int num_sms);
+size_t br_quad_smem_bytes();
 size_t br_pair_smem_bytes();
 cudaError_t launch_bsk_to_ntt(const uint32_t *bsk, uint32_t *bsk_hat, int n, const uint2 *tw_lane, uint32_t scale0,
                               uint32_t scale1, int num_sms, cudaStream_t st);

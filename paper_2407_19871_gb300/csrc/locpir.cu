@@ -185,6 +185,7 @@ extern "C" int lp_create(const lp_params *p, int device, lp_ctx **out)
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->br_pair_clusters = br_pair_clusters(c->num_sms);
+    c->br_quad_clusters = br_quad_clusters(c->num_sms);
     build_ntt_tables(c->tables);
     if ((e = upload_constants(c->tables)) != cudaSuccess) {
         delete c;
@@ -419,6 +420,7 @@ int lp::br_variant(const lp_ctx *c)
     case LP_BR_NTT_BATCHED: return BR_VARIANT_BATCHED;
     case LP_BR_NTT_SPLIT: return BR_VARIANT_SPLIT;
     case LP_BR_NTT_PAIR: return BR_VARIANT_PAIR;
+    case LP_BR_NTT_QUAD: return BR_VARIANT_QUAD;
     default: return BR_VARIANT_AUTO;
     }
 }
@@ -438,7 +440,7 @@ int lp::run_br(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st)
                               static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
                               static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n, (int)jobs, mu,
                               static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max,
-                              c->br_tail_split, br_pair_limit(c), &launched);
+                              c->br_tail_split, br_pair_limit(c), br_quad_limit(c), &launched);
     timer_end(c, "br", st, ev0);
     c->launches += launched;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
@@ -467,7 +469,7 @@ int lp::run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32
 extern "C" int lp_set_engines(lp_ctx *c, int br_engine, int ks_engine)
 {
     if (!c) return fail(LP_EINVAL, "null context");
-    if (br_engine < LP_BR_NTT || br_engine > LP_BR_NTT_PAIR)
+    if (br_engine < LP_BR_NTT || br_engine > LP_BR_NTT_QUAD)
         return fail(LP_EINVAL, "unknown blind-rotation engine %d", br_engine);
     if (ks_engine < LP_KS_TABLE || ks_engine > LP_KS_TENSOR_INT8)
         return fail(LP_EINVAL, "unknown key-switch engine %d", ks_engine);
@@ -565,6 +567,26 @@ static int measure_tuning(lp_ctx *c, lp_tuning *t)
         if (e != cudaSuccess) return cuda_fail(e, "autotune paired blind rotation");
         if (tp[1] < tp[0]) t->pair_max = pc;
     }
+    // Quad against the faster of paired and split at one ciphertext per resident cluster of four.
+    t->quad_max = -1;
+    const int qc = c->br_quad_clusters;
+    if (qc > 0) {
+        float tq[2] = {};
+        for (int v = 0; v < 2 && e == cudaSuccess; v++) {
+            const int variant = v ? BR_VARIANT_QUAD : (t->pair_max > 0 ? BR_VARIANT_PAIR : BR_VARIANT_SPLIT);
+            e = time_median(
+                [&] {
+                    c->launches++;
+                    return launch_br(static_cast<const uint16_t *>(c->abar.ptr), stride,
+                                     static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                                     static_cast<const uint2 *>(c->tw_lane.ptr), n, qc, T_EIGHTH,
+                                     static_cast<int *>(c->err.ptr), S, 0, variant);
+                },
+                &tq[v]);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "autotune quad blind rotation");
+        if (tq[1] < tq[0]) t->quad_max = qc;
+    }
     // Key switch: sliced against whole-table CTAs at 1/4 .. 1 batch per SM (64 outputs each),
     // on the extracted samples the blind rotations just wrote.
     DevBuf out;
@@ -603,6 +625,7 @@ static void apply_tuning(lp_ctx *c, const lp_tuning &t)
     c->br_tail_split = t.tail_split;
     c->ks_slice_max = t.ks_slice_max;
     c->br_pair_max = t.pair_max;
+    c->br_quad_max = t.quad_max;
 }
 
 extern "C" int lp_autotune(lp_ctx *c, int *split_max_out)
@@ -656,17 +679,19 @@ static bool read_tuning(const char *path, const std::string &key, lp_tuning *t)
         return end != txt.c_str() + p;
     };
     std::string k;
-    long sm = 0, ts = 0, ks = 0, pm = 0;
+    long sm = 0, ts = 0, ks = 0, pm = 0, qm = 0;
     if (!field("key", &k, nullptr) || k != key) return false;
     if (!field("split_max", nullptr, &sm) || !field("tail_split", nullptr, &ts) || !field("ks_slice_max", nullptr, &ks) ||
-        !field("pair_max", nullptr, &pm))
+        !field("pair_max", nullptr, &pm) || !field("quad_max", nullptr, &qm))
         return false;
-    if (sm < 1 || sm > 1 << 20 || (ts != 0 && ts != 1) || ks < -1 || ks > 1 << 20 || pm < -1 || pm > 1 << 20)
+    if (sm < 1 || sm > 1 << 20 || (ts != 0 && ts != 1) || ks < -1 || ks > 1 << 20 || pm < -1 || pm > 1 << 20 ||
+        qm < -1 || qm > 1 << 20)
         return false;
     t->split_max = (int)sm;
     t->tail_split = (int)ts;
     t->ks_slice_max = (int)ks;
     t->pair_max = (int)pm;
+    t->quad_max = (int)qm;
     return true;
 }
 
@@ -677,8 +702,10 @@ static int write_tuning(const char *path, const std::string &key, const lp_tunin
     if (!f) return fail(LP_EINVAL, "cannot write the tuning cache %s", tmp.c_str());
     std::string k;
     for (char ch : key) k += (ch == '"' || ch == '\\') ? '_' : ch;
-    fprintf(f, "{\"key\": \"%s\", \"split_max\": %d, \"tail_split\": %d, \"ks_slice_max\": %d, \"pair_max\": %d}\n",
-            k.c_str(), t.split_max, t.tail_split, t.ks_slice_max, t.pair_max);
+    fprintf(f,
+            "{\"key\": \"%s\", \"split_max\": %d, \"tail_split\": %d, \"ks_slice_max\": %d, \"pair_max\": %d, "
+            "\"quad_max\": %d}\n",
+            k.c_str(), t.split_max, t.tail_split, t.ks_slice_max, t.pair_max, t.quad_max);
     const bool ok = fclose(f) == 0;
     if (!ok || rename(tmp.c_str(), path) != 0) return fail(LP_EINVAL, "cannot write the tuning cache %s", path);
     return LP_OK;
@@ -724,9 +751,10 @@ extern "C" int lp_set_executor(lp_ctx *c, int executor)
 extern "C" int lp_set_tuning(lp_ctx *c, const lp_tuning *t)
 {
     if (!c || !t) return fail(LP_EINVAL, "null argument");
-    if (t->split_max < 0 || (t->tail_split != 0 && t->tail_split != 1) || t->ks_slice_max < -1 || t->pair_max < -1)
-        return fail(LP_EINVAL, "invalid tuning (split_max %d, tail_split %d, ks_slice_max %d, pair_max %d)",
-                    t->split_max, t->tail_split, t->ks_slice_max, t->pair_max);
+    if (t->split_max < 0 || (t->tail_split != 0 && t->tail_split != 1) || t->ks_slice_max < -1 || t->pair_max < -1 ||
+        t->quad_max < -1)
+        return fail(LP_EINVAL, "invalid tuning (split_max %d, tail_split %d, ks_slice_max %d, pair_max %d, quad_max %d)",
+                    t->split_max, t->tail_split, t->ks_slice_max, t->pair_max, t->quad_max);
     apply_tuning(c, *t);
     return LP_OK;
 }
@@ -739,6 +767,7 @@ extern "C" int lp_get_tuning(const lp_ctx *c, lp_tuning *t)
     t->tail_split = c->br_tail_split;
     t->ks_slice_max = c->ks_slice_max;
     t->pair_max = c->br_pair_max;
+    t->quad_max = c->br_quad_max;
     return LP_OK;
 }
 
@@ -994,6 +1023,25 @@ extern "C" int lp_selftest_pair_timeout(lp_ctx *c, void *stream)
     c->launches++;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? LP_OK : cuda_fail(e, "paired-kernel self-test");
+}
+
+extern "C" int lp_selftest_quad_timeout(lp_ctx *c, void *stream)
+{
+    if (!c) return fail(LP_EINVAL, "null context");
+    if (!c->have_bsk) return fail(LP_ENOKEY, "load the bootstrapping key first");
+    cudaSetDevice(c->device);
+    int rc = ensure_scratch(c, 1);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(c->abar.ptr, 0, (size_t)abar_stride(c) * sizeof(uint16_t), st);
+    if (e == cudaSuccess)
+        e = launch_quad_selftest(static_cast<const uint16_t *>(c->abar.ptr), abar_stride(c),
+                                 static_cast<uint32_t *>(c->ext.ptr), static_cast<const uint32_t *>(c->bsk_hat.ptr),
+                                 static_cast<const uint2 *>(c->tw_lane.ptr), c->params.n,
+                                 static_cast<int *>(c->err.ptr), c->num_sms, st);
+    c->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? LP_OK : cuda_fail(e, "quad-kernel self-test");
 }
 
 extern "C" int lp_selftest_wait_timeout(lp_ctx *c, uint32_t limit_ms, void *stream)

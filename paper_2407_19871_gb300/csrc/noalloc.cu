@@ -90,13 +90,14 @@ extern "C" int lp_gate_batch_noalloc(lp_ctx *c, int op, const uint32_t *a, const
     e = launch_precomb_dense(op, a, b, op == LP_MUX ? cc : nullptr, n, count, abar, abar_stride(c), c->num_sms, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "pre-combination launch");
-    // The NTT kernels only: a forced batched, split or paired choice is honoured, and a
+    // The NTT kernels only: a forced batched, split, paired or quad choice is honoured, and a
     // tensor-core engine selection falls back to the automatic NTT choice (those engines
     // allocate).
     const int variant = br_variant(c);
     e = launch_br(abar, abar_stride(c), ext, static_cast<const uint32_t *>(c->bsk_hat.ptr),
                   static_cast<const uint2 *>(c->tw_lane.ptr), n, (int)(count * halves), T_EIGHTH,
-                  static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max, 0, br_pair_limit(c));
+                  static_cast<int *>(c->err.ptr), c->num_sms, st, variant, c->br_split_max, 0, br_pair_limit(c),
+                  br_quad_limit(c));
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "blind rotation launch");
     e = launch_ks(ext, nullptr, count, op == LP_MUX, out, static_cast<const uint32_t *>(c->ksk.ptr), n,

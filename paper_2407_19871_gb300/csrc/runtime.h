@@ -47,6 +47,8 @@ struct lp_ctx {
     int br_tail_split = 0;          // a wider level's partial last wave runs split (lp_autotune)
     int br_pair_max = 0;            // paired-kernel limit as set (0: resident clusters, -1: never)
     int br_pair_clusters = 0;       // clusters of the paired kernel resident at once
+    int br_quad_max = 0;            // quad-kernel limit as set (0: resident clusters, -1: never)
+    int br_quad_clusters = 0;       // clusters of the quad kernel resident at once
     int ks_slice_max = 0;           // key switches of at most this many batches run sliced (0: rule)
     int executor = LP_EXEC_LEVELS;  // circuits: per-level kernels or the persistent executor
     void *blas = nullptr;           // cuBLAS handle, created on first use
@@ -74,6 +76,11 @@ int br_variant(const lp_ctx *c);
 inline int br_pair_limit(const lp_ctx *c)
 {
     return c->br_pair_max == 0 ? c->br_pair_clusters : c->br_pair_max < 0 ? 0 : c->br_pair_max;
+}
+// Widest level (or remainder) that runs on the quad kernel; 0 = none.
+inline int br_quad_limit(const lp_ctx *c)
+{
+    return c->br_quad_max == 0 ? c->br_quad_clusters : c->br_quad_max < 0 ? 0 : c->br_quad_max;
 }
 int run_ks(lp_ctx *c, const KsJob *jobs, size_t njobs, int dense_mux, uint32_t *out, cudaStream_t st);
 int run_br_tensor(lp_ctx *c, size_t jobs, uint32_t mu, cudaStream_t st);

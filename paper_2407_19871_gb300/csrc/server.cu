@@ -231,7 +231,7 @@ static int tick(Server &S)
             e = launch_br(static_cast<const uint16_t *>(S.abar.ptr), abar_stride(c), static_cast<uint32_t *>(S.ext.ptr),
                           static_cast<const uint32_t *>(c->bsk_hat.ptr), static_cast<const uint2 *>(c->tw_lane.ptr), n,
                           (int)p.br_cnt, T_EIGHTH, static_cast<int *>(c->err.ptr), c->num_sms, S.st,
-                          BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, br_pair_limit(c), &lb);
+                          BR_VARIANT_AUTO, c->br_split_max, c->br_tail_split, br_pair_limit(c), br_quad_limit(c), &lb);
         if (e == cudaSuccess)
             e = launch_ks(static_cast<const uint32_t *>(S.ext.ptr), dks + p.ks_off, p.ks_cnt, 0, pool,
                           static_cast<const uint32_t *>(c->ksk.ptr), n, static_cast<int *>(c->err.ptr), c->num_sms,

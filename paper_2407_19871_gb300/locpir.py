@@ -35,9 +35,9 @@ EXPORTS = [
     "lp_save_keys_file", "lp_verify_keys_file", "lp_load_keys_file", "lp_sha256",
     "lp_plan_locpir", "lp_plan_run", "lp_plan_info", "lp_plan_destroy", "lp_set_engines", "lp_autotune",
     "lp_plan_locpir_known", "lp_circuit_info", "lp_autotune_cached", "lp_set_tuning", "lp_get_tuning",
-    "lp_set_executor", "lp_selftest_exec_timeout", "lp_selftest_pair_timeout",
+    "lp_set_executor", "lp_selftest_exec_timeout", "lp_selftest_pair_timeout", "lp_selftest_quad_timeout",
 ]
-LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT, LP_BR_NTT_PAIR = 0, 1, 2, 3, 4, 5
+LP_BR_NTT, LP_BR_TENSOR_BF16, LP_BR_TENSOR_INT8, LP_BR_NTT_BATCHED, LP_BR_NTT_SPLIT, LP_BR_NTT_PAIR, LP_BR_NTT_QUAD = range(7)
 LP_KS_TABLE, LP_KS_TENSOR_INT8 = 0, 1
 LP_SERVER_QUEUE, LP_SERVER_REJECT = 0, 1
 LP_EXEC_LEVELS, LP_EXEC_PERSISTENT = 0, 1
@@ -72,7 +72,8 @@ class lp_circuit_stats(ctypes.Structure):
 
 
 class lp_tuning(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_int) for k in ("split_max", "tail_split", "ks_slice_max", "from_cache", "pair_max")]
+    _fields_ = [(k, ctypes.c_int) for k in ("split_max", "tail_split", "ks_slice_max", "from_cache", "pair_max",
+                                            "quad_max")]
 
 
 class LocpirError(RuntimeError):
@@ -150,6 +151,7 @@ def lib() -> ctypes.CDLL:
             "lp_set_executor": (i, [vp, i]),
             "lp_selftest_exec_timeout": (i, [vp, vp]),
             "lp_selftest_pair_timeout": (i, [vp, vp]),
+            "lp_selftest_quad_timeout": (i, [vp, vp]),
             "lp_get_tuning": (i, [vp, ctypes.POINTER(lp_tuning)]),
             "lp_circuit_info": (i, [i, i, i, i, i, vp, ctypes.POINTER(lp_circuit_stats)]),
         }
@@ -413,8 +415,9 @@ class Context:
         _check(lib().lp_autotune_cached(self.h, path, int(force), ctypes.byref(t)), "lp_autotune_cached")
         return {k: getattr(t, k) for k, _ in lp_tuning._fields_}
 
-    def lp_set_tuning(self, split_max: int = 0, tail_split: int = 0, ks_slice_max: int = 0, pair_max: int = 0) -> None:
-        t = lp_tuning(split_max, tail_split, ks_slice_max, 0, pair_max)
+    def lp_set_tuning(self, split_max: int = 0, tail_split: int = 0, ks_slice_max: int = 0, pair_max: int = 0,
+                      quad_max: int = 0) -> None:
+        t = lp_tuning(split_max, tail_split, ks_slice_max, 0, pair_max, quad_max)
         _check(lib().lp_set_tuning(self.h, ctypes.byref(t)), "lp_set_tuning")
 
     def lp_selftest_exec_timeout(self, stream=None) -> None:
@@ -422,6 +425,9 @@ class Context:
 
     def lp_selftest_pair_timeout(self, stream=None) -> None:
         _check(lib().lp_selftest_pair_timeout(self.h, _stream(stream)), "lp_selftest_pair_timeout")
+
+    def lp_selftest_quad_timeout(self, stream=None) -> None:
+        _check(lib().lp_selftest_quad_timeout(self.h, _stream(stream)), "lp_selftest_quad_timeout")
 
     def lp_set_executor(self, executor: int) -> None:
         _check(lib().lp_set_executor(self.h, executor), "lp_set_executor")

@@ -30,10 +30,11 @@ def test_cache_roundtrip(tuned_ctx, tmp_path):
     assert rec["split_max"] == first["split_max"] >= 1
     second = tuned_ctx.lp_autotune_cached(str(path))
     assert second == dict(first, from_cache=1)
-    assert tuned_ctx.lp_get_tuning() == {k: first[k] for k in ("split_max", "tail_split", "ks_slice_max", "pair_max")}
-    assert rec["pair_max"] == first["pair_max"] >= -1
+    assert tuned_ctx.lp_get_tuning() == {k: first[k] for k in ("split_max", "tail_split", "ks_slice_max", "pair_max",
+                                                                "quad_max")}
+    assert rec["pair_max"] == first["pair_max"] >= -1 and rec["quad_max"] == first["quad_max"] >= -1
     # an entry for another device is not used: the call measures again and rewrites the file
-    rec["key"] = "another GPU|sms=1|n=630|schema=2"
+    rec["key"] = "another GPU|sms=1|n=630|schema=3"
     path.write_text(json.dumps(rec))
     third = tuned_ctx.lp_autotune_cached(str(path))
     assert third["from_cache"] == 0
@@ -42,8 +43,8 @@ def test_cache_roundtrip(tuned_ctx, tmp_path):
 
 def test_policies_give_identical_bits(tuned_ctx, keys):
     """NAND gates over 4 ciphertexts per SM plus a 200-wide remainder: all batched under the
-    built-in rules, the remainder split (or paired, each cluster taking several ciphertexts in
-    turn) under tail splitting; and key switches of 1-4 batches per SM whole-table and sliced.
+    built-in rules, the remainder split (or paired, or quad, each cluster taking several
+    ciphertexts in turn) under tail splitting; and key switches of 1-4 batches per SM whole-table and sliced.
     Every output word is the same; a sample is the oracle's."""
     from paper_2407_19871_gb300.locpir import LP_NAND
     p = keys.params
@@ -56,7 +57,8 @@ def test_policies_give_identical_bits(tuned_ctx, keys):
     outs = []
     for policy in (dict(split_max=0, tail_split=0, ks_slice_max=0),        # built-in rules
                    dict(split_max=2 * sms, tail_split=1, ks_slice_max=0, pair_max=-1),  # remainder split
-                   dict(split_max=2 * sms, tail_split=1, ks_slice_max=-1, pair_max=200),  # remainder paired
+                   dict(split_max=2 * sms, tail_split=1, ks_slice_max=-1, pair_max=200, quad_max=-1),  # paired
+                   dict(split_max=2 * sms, tail_split=1, ks_slice_max=0, pair_max=-1, quad_max=200),  # quad
                    dict(split_max=sms, tail_split=0, ks_slice_max=sms)):   # always slice here
         tuned_ctx.lp_set_tuning(**policy)
         out = empty_dev(count, p.n + 1)

@@ -98,17 +98,19 @@ def edge_case(request):
     ctx.close()
 
 
-@pytest.mark.parametrize("engine", ["batched", "split", "pair"])
+@pytest.mark.parametrize("engine", ["batched", "split", "pair", "quad"])
 @pytest.mark.parametrize("count", [1, 7])
 def test_bootstrap_at_the_crt_edge_matches_oracle(edge_case, engine, count):
     """count = 7: one full group of 4 and a ragged group of 3 on the batched kernel; sample 0
     has one edge step, sample 1 all 630, the others a random subset."""
     from crt_edge import MU_EDGE, crafted_lwes
-    from paper_2407_19871_gb300.locpir import LP_BR_NTT, LP_BR_NTT_BATCHED, LP_BR_NTT_PAIR, LP_BR_NTT_SPLIT
+    from paper_2407_19871_gb300.locpir import (LP_BR_NTT, LP_BR_NTT_BATCHED, LP_BR_NTT_PAIR, LP_BR_NTT_QUAD,
+                                               LP_BR_NTT_SPLIT)
     ctx, keys = edge_case
     p = keys.params
     lwe = crafted_lwes(p, count, seed=40 + count)
-    ctx.lp_set_engines({"batched": LP_BR_NTT_BATCHED, "split": LP_BR_NTT_SPLIT, "pair": LP_BR_NTT_PAIR}[engine], 0)
+    ctx.lp_set_engines({"batched": LP_BR_NTT_BATCHED, "split": LP_BR_NTT_SPLIT, "pair": LP_BR_NTT_PAIR,
+                        "quad": LP_BR_NTT_QUAD}[engine], 0)
     try:
         ext = empty_dev(count, p.N + 1)
         ctx.lp_bootstrap_extract(to_dev(lwe), MU_EDGE, ext, count)

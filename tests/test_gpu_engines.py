@@ -84,15 +84,16 @@ def test_gates_all_engine_pairs_agree(engines_ctx, keys, op):
 def test_unknown_engine_is_rejected(engines_ctx):
     from paper_2407_19871_gb300.locpir import LocpirError
     with pytest.raises(LocpirError):
-        engines_ctx.lp_set_engines(6, 0)
+        engines_ctx.lp_set_engines(7, 0)
     with pytest.raises(LocpirError):
         engines_ctx.lp_set_engines(0, 2)
 
 
-@pytest.mark.parametrize("variant", [3, 4, 5])
+@pytest.mark.parametrize("variant", [3, 4, 5, 6])
 def test_ntt_variants_match_oracle(engines_ctx, keys, variant):
-    """The batched (4 ciphertexts per CTA), split (12 warps per ciphertext) and paired (two CTAs
-    per ciphertext) NTT kernels, forced, on one full group plus a ragged one."""
+    """The batched (4 ciphertexts per CTA), split (12 warps per ciphertext), paired (two CTAs per
+    ciphertext) and quad (four CTAs per ciphertext) NTT kernels, forced, on one full group plus
+    a ragged one."""
     p = keys.params
     lwe = _random_lwes(61 + variant, 7, p.n)
     engines_ctx.lp_set_engines(variant, 0)

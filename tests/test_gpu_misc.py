@@ -89,7 +89,8 @@ def test_lwe_dimension_edges_match_oracle(n):
                    for k, X in enumerate((A, B, Cb)))
         for op in (oracle.AND, oracle.MUX):
             want = oracle.gate_batch(kn, op, a, b, c if op == oracle.MUX else None)
-            for variant in (locpir.LP_BR_NTT_BATCHED, locpir.LP_BR_NTT_SPLIT, locpir.LP_BR_NTT_PAIR):
+            for variant in (locpir.LP_BR_NTT_BATCHED, locpir.LP_BR_NTT_SPLIT, locpir.LP_BR_NTT_PAIR,
+                            locpir.LP_BR_NTT_QUAD):
                 ctx.lp_set_engines(variant, 0)
                 out = empty_dev(cnt, p.n + 1)
                 ctx.lp_gate_batch(op, to_dev(a), to_dev(b), to_dev(c) if op == oracle.MUX else None, out, cnt)
