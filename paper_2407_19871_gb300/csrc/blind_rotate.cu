@@ -30,9 +30,9 @@
 // swaps half of its residues through shared memory: the prime-0 warp recombines component 0
 // (centred CRT) and adds it to ACC, the prime-1 warp component 1.
 //
-// The file also holds br_split_kernel, which spreads one ciphertext over 12 warps for levels
-// too small to fill the GPU (see its section), and launch_br, which picks one of the two per
-// level.
+// The file also holds the kernels for levels too small to fill the GPU (see their sections):
+// br_split_kernel spreads one ciphertext over 12 warps, br_pair_kernel over a cluster of two
+// CTAs and br_quad_kernel over a cluster of four; launch_br picks one per level.
 #include "common.cuh"
 #include "kernels.h"
 #include "ks_device.cuh"
